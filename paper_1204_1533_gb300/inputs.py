@@ -1,0 +1,383 @@
+"""Seeded synthetic inputs: node sets, meshes and initial states.
+
+This module produces the *data* that both the CUDA library and its CPU test
+oracle consume: the 1-D solution-node set {s_i}, isoparametric node
+coordinates of structured quad/hex meshes (optionally perturbed, curved,
+periodic, or with per-element re-oriented local coordinates), boundary tags,
+and nodal initial / manufactured states. It evaluates nothing of the Line-DG
+scheme itself (no quadrature, no basis, no metric, no flux, no residual).
+
+Mesh dictionaries have the keys
+  D         : int, 2 or 3
+  p         : int, polynomial degree
+  s         : float64[p+1], increasing node set on [0,1], s[0]=0, s[p]=1,
+              symmetric (s[p-i] == 1 - s[i] exactly)
+  nodes     : float64[E, (p+1)^D, D], node coordinates x_ijk, local node index
+              i + (p+1) j + (p+1)^2 k (i runs along reference direction 1)
+  vertices  : int64[E, 2^D] global vertex ids; local corner c sits at the
+              reference corner (c & 1, (c >> 1) & 1, (c >> 2) & 1); periodic
+              images share ids
+  btag      : int32[E, 2D]; face f = 2 d + end (end 0 at X_d = 0, end 1 at
+              X_d = 1); -1 = interior (matched through vertex ids), >= 0 =
+              boundary tag
+Elements of the structured generators are numbered e = ex + nx (ey + ny ez).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+MESH_SEED = 1204
+STATE_SEED = 1533
+
+
+# ---------------------------------------------------------------------------
+# node sets
+# ---------------------------------------------------------------------------
+def gll_nodes(p: int) -> np.ndarray:
+    """Gauss-Lobatto-Legendre points mapped to [0,1] (the node set chosen for
+    s_i; the paper only requires an increasing set with s_0=0, s_p=1).
+    Made exactly symmetric so that reversed face orientations map node i to
+    node p-i."""
+    if p < 1:
+        raise ValueError("p >= 1 required")
+    from numpy.polynomial import legendre as leg
+    c = np.zeros(p + 1)
+    c[p] = 1.0
+    inner = np.sort(np.real(leg.legroots(leg.legder(c)))) if p >= 2 else np.zeros(0)
+    x = np.concatenate([[-1.0], inner, [1.0]])
+    s = 0.5 * (x + 1.0)
+    s[0], s[p] = 0.0, 1.0
+    for i in range(1, (p + 1) // 2):
+        s[p - i] = 1.0 - s[i]
+    if p % 2 == 0:
+        s[p // 2] = 0.5
+    return s
+
+
+def equispaced_nodes(p: int) -> np.ndarray:
+    s = np.linspace(0.0, 1.0, p + 1)
+    for i in range(1, (p + 1) // 2):
+        s[p - i] = 1.0 - s[i]
+    if p % 2 == 0:
+        s[p // 2] = 0.5
+    return s
+
+
+# ---------------------------------------------------------------------------
+# structured meshes
+# ---------------------------------------------------------------------------
+def _corner_bits(D):
+    return [tuple((c >> b) & 1 for b in range(D)) for c in range(1 << D)]
+
+
+def structured_mesh(n, p, lo, hi, periodic, perturb=0.0, seed=MESH_SEED,
+                    node_map=None, s=None, btag_of_face=None, ycoords=None):
+    """Tensor-product mesh of len(n) dimensions.
+
+    n        : elements per dimension
+    lo, hi   : domain box
+    periodic : per-dimension periodicity flags (periodic images share ids)
+    perturb  : vertex perturbation, a fraction of the local spacing h; every
+               coordinate of every perturbable vertex moves by U(-perturb h,
+               +perturb h). A vertex is perturbable when it is interior in
+               every non-periodic dimension; periodic perturbations repeat.
+    node_map : optional callable (xyz[..., D]) -> xyz applied to the node
+               coordinates after multilinear placement (curved elements)
+    btag_of_face(d, end) -> tag for faces on non-periodic domain sides
+    ycoords  : optional explicit vertex coordinates along dimension 1
+    """
+    D = len(n)
+    n = tuple(int(v) for v in n)
+    s = gll_nodes(p) if s is None else np.asarray(s, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    nv = [n[d] if periodic[d] else n[d] + 1 for d in range(D)]
+    h = [(hi[d] - lo[d]) / n[d] for d in range(D)]
+    # vertex perturbations on the id grid (periodic images identical)
+    shape_ids = tuple(nv[::-1])  # [z][y][x]
+    delta = rng.uniform(-1.0, 1.0, size=shape_ids + (D,))
+    movable = np.ones(shape_ids, dtype=bool)
+    for d in range(D):
+        if not periodic[d]:
+            ax = D - 1 - d
+            sl = [slice(None)] * D
+            sl[ax] = 0
+            movable[tuple(sl)] = False
+            sl[ax] = nv[d] - 1
+            movable[tuple(sl)] = False
+    for d in range(D):
+        delta[..., d] *= perturb * h[d]
+    delta[~movable] = 0.0
+
+    def coord_axis(d, idx):
+        if d == 1 and ycoords is not None:
+            return ycoords[idx]
+        return lo[d] + idx * h[d]
+
+    E = int(np.prod(n))
+    npe = (p + 1) ** D
+    nodes = np.zeros((E, npe, D))
+    verts = np.zeros((E, 1 << D), dtype=np.int64)
+    btag = -np.ones((E, 2 * D), dtype=np.int32)
+    corners = _corner_bits(D)
+    # reference node coordinates, local index i + (p+1) j + (p+1)^2 k
+    ref = np.array([[s[(a // (p + 1) ** b) % (p + 1)] for b in range(D)]
+                    for a in range(npe)])
+    for e, eidx in enumerate(itertools.product(*[range(n[d]) for d in reversed(range(D))])):
+        eidx = eidx[::-1]  # (ex, ey, ez)
+        cpos = np.zeros((1 << D, D))
+        for c, bits in enumerate(corners):
+            g = [eidx[d] + bits[d] for d in range(D)]
+            gid = [g[d] % nv[d] if periodic[d] else g[d] for d in range(D)]
+            vid = 0
+            for d in reversed(range(D)):
+                vid = vid * nv[d] + gid[d]
+            verts[e, c] = vid
+            dl = delta[tuple(gid[::-1])]
+            for d in range(D):
+                cpos[c, d] = coord_axis(d, g[d]) + dl[d]
+        # multilinear placement of the nodes between the corners
+        w = np.ones((npe, 1 << D))
+        for c, bits in enumerate(corners):
+            for d in range(D):
+                w[:, c] *= ref[:, d] if bits[d] else (1.0 - ref[:, d])
+        nodes[e] = w @ cpos
+        for d in range(D):
+            if periodic[d]:
+                continue
+            if eidx[d] == 0:
+                btag[e, 2 * d] = 0 if btag_of_face is None else btag_of_face(d, 0)
+            if eidx[d] == n[d] - 1:
+                btag[e, 2 * d + 1] = 0 if btag_of_face is None else btag_of_face(d, 1)
+    if node_map is not None:
+        nodes = node_map(nodes)
+    return {"D": D, "p": int(p), "s": s, "nodes": np.ascontiguousarray(nodes),
+            "vertices": verts, "btag": btag,
+            "shape": n, "periodic": tuple(bool(x) for x in periodic),
+            "lo": tuple(lo), "hi": tuple(hi)}
+
+
+# ---------------------------------------------------------------------------
+# per-element re-orientation (exercises general face orientations)
+# ---------------------------------------------------------------------------
+def _rotations(D):
+    """Orientation-preserving symmetries of the reference square / cube as
+    (perm, flip): new axis a takes old axis perm[a], reversed if flip[a]."""
+    out = []
+    for perm in itertools.permutations(range(D)):
+        inv = sum(1 for i in range(D) for j in range(i + 1, D) if perm[i] > perm[j])
+        for flip in itertools.product([0, 1], repeat=D):
+            if (inv + sum(flip)) % 2 == 0:
+                out.append((perm, flip))
+    return out
+
+
+def reorient(mesh, seed=MESH_SEED + 7):
+    """Give each element a random orientation-preserving local coordinate
+    system. Returns (new_mesh, maps) where maps[e] is the node permutation
+    new_local -> old_local, usable with permute_nodal()."""
+    D, p = mesh["D"], mesh["p"]
+    rng = np.random.default_rng(seed)
+    rots = _rotations(D)
+    E = mesh["nodes"].shape[0]
+    npe = (p + 1) ** D
+    nodes = np.empty_like(mesh["nodes"])
+    verts = np.empty_like(mesh["vertices"])
+    btag = np.empty_like(mesh["btag"])
+    maps = np.empty((E, npe), dtype=np.int64)
+    for e in range(E):
+        perm, flip = rots[rng.integers(len(rots))]
+        for a in range(npe):
+            newidx = [(a // (p + 1) ** b) % (p + 1) for b in range(D)]
+            old = [0] * D
+            for ax in range(D):
+                v = newidx[ax]
+                old[perm[ax]] = (p - v) if flip[ax] else v
+            maps[e, a] = sum(old[b] * (p + 1) ** b for b in range(D))
+        nodes[e] = mesh["nodes"][e][maps[e]]
+        for c in range(1 << D):
+            newb = [(c >> b) & 1 for b in range(D)]
+            old = [0] * D
+            for ax in range(D):
+                old[perm[ax]] = (1 - newb[ax]) if flip[ax] else newb[ax]
+            verts[e, c] = mesh["vertices"][e, sum(old[b] << b for b in range(D))]
+        for ax in range(D):
+            for end in range(2):
+                oend = (1 - end) if flip[ax] else end
+                btag[e, 2 * ax + end] = mesh["btag"][e, 2 * perm[ax] + oend]
+    out = dict(mesh)
+    out.update(nodes=nodes, vertices=verts, btag=btag)
+    out.pop("shape", None)
+    return out, maps
+
+
+def permute_nodal(field, maps):
+    """Apply reorient() node maps to a nodal field [E, ..., (p+1)^D]."""
+    out = np.empty_like(field)
+    for e in range(field.shape[0]):
+        out[e] = field[e][..., maps[e]]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# workload meshes (sizes and perturbations of the benchmark configurations)
+# ---------------------------------------------------------------------------
+def poisson_square_mesh(n=8, p=3, perturb=0.15, seed=MESH_SEED):
+    """Unit square, n x n straight-sided quads, interior vertices perturbed by
+    U(-perturb h, +perturb h); all sides Dirichlet (tag 0)."""
+    return structured_mesh((n, n), p, (0.0, 0.0), (1.0, 1.0), (False, False),
+                           perturb=perturb, seed=seed)
+
+
+def vortex_mesh(n=64, p=4, L=10.0, perturb=0.1, seed=MESH_SEED):
+    """Periodic [0,L]^2, n x n quads, all vertices perturbed by U(-0.1h,0.1h)."""
+    return structured_mesh((n, n), p, (0.0, 0.0), (L, L), (True, True),
+                           perturb=perturb, seed=seed)
+
+
+def tgv_node_map(amp=0.05):
+    def f(x):
+        y = np.empty_like(x)
+        y[..., 0] = x[..., 0] + amp * np.sin(x[..., 1]) * np.sin(x[..., 2])
+        y[..., 1] = x[..., 1] + amp * np.sin(x[..., 2]) * np.sin(x[..., 0])
+        y[..., 2] = x[..., 2] + amp * np.sin(x[..., 0]) * np.sin(x[..., 1])
+        return y
+    return f
+
+
+def tgv_mesh(n=32, p=3, amp=0.05):
+    """Periodic [0,2pi]^3, n^3 hexes, nodes curved by the cyclic map
+    x + amp sin(y) sin(z)."""
+    L = 2.0 * math.pi
+    return structured_mesh((n, n, n), p, (0.0, 0.0, 0.0), (L, L, L), (True, True, True),
+                           node_map=tgv_node_map(amp))
+
+
+def channel_wall_coords(ny=32, ratio=1.1):
+    """Vertex y-coordinates on [-1,1], geometric growth `ratio` from each wall."""
+    half = ny // 2
+    dy = np.array([ratio ** k for k in range(half)])
+    dy /= dy.sum()
+    y = np.concatenate([[-1.0], -1.0 + np.cumsum(dy)])
+    y[-1] = 0.0
+    return np.concatenate([y, -y[-2::-1]])
+
+
+def channel_mesh(nx=64, ny=32, nz=32, p=4, amp=0.1, wavelength=1.0, ratio=1.1):
+    """[0,4] x [-1,1] x [0,2] channel, periodic in x and z, walls (tag 1) at
+    y = +-1 + amp sin(2 pi x / wavelength) blended linearly to the centre line,
+    wall-normal geometric stretching `ratio` from each wall."""
+    yc = channel_wall_coords(ny, ratio)
+
+    def bump(x):
+        y = x.copy()
+        y[..., 1] = x[..., 1] + amp * np.sin(2 * math.pi * x[..., 0] / wavelength) * np.abs(x[..., 1])
+        return y
+    return structured_mesh((nx, ny, nz), p, (0.0, -1.0, 0.0), (4.0, 1.0, 2.0), (True, False, True),
+                           node_map=bump, ycoords=yc, btag_of_face=lambda d, end: 1)
+
+
+# ---------------------------------------------------------------------------
+# states (conserved variables, layout [E, n_c, (p+1)^D])
+# ---------------------------------------------------------------------------
+def _to_conserved(rho, vel, p, gamma):
+    E_ = p / (gamma - 1.0) + 0.5 * rho * sum(v * v for v in vel)
+    return np.stack([rho] + [rho * v for v in vel] + [E_], axis=1)
+
+
+def vortex_state(mesh, gamma=1.4, mach=0.5, eps=5.0, rc=1.0, x0=5.0, y0=5.0,
+                 theta=math.atan(0.5), t=0.0):
+    """Isentropic vortex of the Euler test (vortex strength eps, size rc),
+    free stream rho=1, |u|=1, p = 1/(gamma M^2)."""
+    x = mesh["nodes"][..., 0]
+    y = mesh["nodes"][..., 1]
+    uinf = 1.0
+    ub, vb = uinf * math.cos(theta), uinf * math.sin(theta)
+    pinf = 1.0 / (gamma * mach ** 2)
+    dx, dy = (x - x0) - ub * t, (y - y0) - vb * t
+    f = (1.0 - dx ** 2 - dy ** 2) / rc ** 2
+    u = uinf * (math.cos(theta) - eps * dy / (2 * math.pi * rc) * np.exp(f / 2))
+    v = uinf * (math.sin(theta) + eps * dx / (2 * math.pi * rc) * np.exp(f / 2))
+    base = 1.0 - eps ** 2 * (gamma - 1.0) * mach ** 2 / (8 * math.pi ** 2) * np.exp(f)
+    rho = base ** (1.0 / (gamma - 1.0))
+    p = pinf * base ** (gamma / (gamma - 1.0))
+    return _to_conserved(rho, [u, v], p, gamma)
+
+
+def tgv_state(mesh, gamma=1.4, mach=0.1, V0=1.0, rho0=1.0):
+    """Single-mode Taylor-Green vortex (L=1), isothermal density."""
+    x, y, z = (mesh["nodes"][..., d] for d in range(3))
+    p0 = rho0 * V0 ** 2 / (gamma * mach ** 2)
+    u = V0 * np.sin(x) * np.cos(y) * np.cos(z)
+    v = -V0 * np.cos(x) * np.sin(y) * np.cos(z)
+    w = np.zeros_like(u)
+    p = p0 + rho0 * V0 ** 2 / 16.0 * (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0)
+    rho = rho0 * p / p0
+    return _to_conserved(rho, [u, v, w], p, gamma)
+
+
+def channel_state(mesh, gamma=1.4, mach=0.3, amp=0.01, seed=STATE_SEED):
+    """Laminar parabolic profile (centre-line speed 1) plus a seeded 1%
+    smooth perturbation; rho = 1, p = 1/(gamma M^2)."""
+    x, y, z = (mesh["nodes"][..., d] for d in range(3))
+    rng = np.random.default_rng(seed)
+    u = np.clip(1.0 - y ** 2, 0.0, None)
+    pert = np.zeros_like(u)
+    for _ in range(4):
+        kx, kz = rng.integers(1, 3, size=2)
+        ph = rng.uniform(0, 2 * math.pi, size=2)
+        pert += np.sin(2 * math.pi * kx * x / 4.0 + ph[0]) * np.sin(math.pi * kz * z + ph[1])
+    u = u * (1.0 + amp * pert)
+    v = amp * pert * np.clip(1.0 - y ** 2, 0.0, None)
+    w = np.zeros_like(u)
+    rho = np.ones_like(u)
+    p = np.full_like(u, 1.0 / (gamma * mach ** 2))
+    return _to_conserved(rho, [u, v, w], p, gamma)
+
+
+def poisson_exact(mesh):
+    """Manufactured u = sin(pi x) sin(pi y), [E, 1, (p+1)^2]."""
+    x, y = mesh["nodes"][..., 0], mesh["nodes"][..., 1]
+    return (np.sin(math.pi * x) * np.sin(math.pi * y))[:, None, :]
+
+
+def poisson_source(mesh):
+    """f = -lap u = 2 pi^2 sin(pi x) sin(pi y)."""
+    return 2.0 * math.pi ** 2 * poisson_exact(mesh)
+
+
+def poisson_exact_grad(mesh):
+    x, y = mesh["nodes"][..., 0], mesh["nodes"][..., 1]
+    gx = math.pi * np.cos(math.pi * x) * np.sin(math.pi * y)
+    gy = math.pi * np.sin(math.pi * x) * np.cos(math.pi * y)
+    return np.stack([gx, gy], axis=1)[:, None, :, :]  # [E, 1, D, nodes]
+
+
+def smooth_perturbation(mesh, state, amp=0.05, seed=STATE_SEED, nmodes=3, periods=None):
+    """state + amp * max|state_c| * (mean of seeded smooth modes), one mode set
+    per component c. periods: per-dimension domain lengths for
+    periodic-compatible wavenumbers (default: the mesh box)."""
+    rng = np.random.default_rng(seed)
+    D = mesh["D"]
+    X = mesh["nodes"]
+    if periods is None:
+        periods = [mesh["hi"][d] - mesh["lo"][d] for d in range(D)]
+    out = state.copy()
+    for c in range(state.shape[1]):
+        m = np.zeros(X.shape[:2])
+        for _ in range(nmodes):
+            k = rng.integers(1, 3, size=D)
+            ph = rng.uniform(0, 2 * math.pi, size=D)
+            term = np.ones(X.shape[:2])
+            for d in range(D):
+                term = term * np.sin(2 * math.pi * k[d] * X[..., d] / periods[d] + ph[d])
+            m += term
+        scale = max(float(np.abs(state[:, c]).max()), 1e-3)
+        out[:, c] = state[:, c] + amp * scale * m / nmodes
+    return out
+
+
+def random_state(shape, seed=STATE_SEED, lo=-1.0, hi=1.0):
+    return np.random.default_rng(seed).uniform(lo, hi, size=shape)

@@ -1,0 +1,169 @@
+"""Pins for the oracle's split matvec, masked preconditioner, ILU(0), GMRES
+and Newton-BDF2 (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1204_1533_gb300 import inputs as I
+from oracle import jacobian as JAC
+from oracle import solvers as S
+from oracle.residual import Discretization, full_residual, gradient
+
+EULER = {"kind": "euler", "gamma": 1.4, "flux": "roe"}
+
+
+def test_line_pattern_counts():
+    # an element's Line-DG block: every node couples to the Dp+1 nodes of its lines
+    for D in (2, 3):
+        for p in (1, 2, 3, 4):
+            pat = S.line_pattern(D, p)
+            assert all(len(r) == D * p + 1 for r in pat)
+            assert all(i in r for i, r in enumerate(pat))
+
+
+def _ns_small():
+    m = I.structured_mesh((3, 3), 2, (0, 0), (1, 1), (True, True), perturb=0.1)
+    m, _ = I.reorient(m)
+    eq = {"kind": "ns", "gamma": 1.4, "flux": "roe", "mu": 0.02, "Pr": 0.72}
+    disc = Discretization(m, eq)
+    npe = disc.npe
+    base = np.zeros((disc.E, 4, npe))
+    base[:, 0], base[:, 1], base[:, 2], base[:, 3] = 1.0, 0.5, -0.2, 1.0 / (1.4 * 0.3 ** 2) / 0.4 + 0.145
+    U = I.smooth_perturbation(m, base, 0.1, periods=[1, 1])
+    return disc, U
+
+
+def test_split_matvec_equals_dense_newton_matrix():
+    disc, U = _ns_small()
+    Q = gradient(disc, U)
+    K11, K12, K21 = JAC.K11(disc, U, Q), JAC.K12(disc, U, Q), JAC.K21(disc)
+    A = JAC.dense_brute_force(lambda X: full_residual(disc, X), U)
+    x = np.random.default_rng(0).standard_normal(U.size)
+    a_dt = 0.7
+    y = S.split_matvec(K11, K12, K21, x, 1.0, -a_dt)
+    assert np.allclose(y, x - a_dt * (A @ x), atol=1e-10 * np.abs(y).max())
+
+
+def test_masked_blocks_keep_in_pattern_product_entries():
+    disc, U = _ns_small()
+    Q = gradient(disc, U)
+    A = (JAC.K11(disc, U, Q) + JAC.K12(disc, U, Q) @ JAC.K21(disc)).toarray()
+    Ab = S.masked_blocks(disc, A, 1.0, -0.3)
+    pat = S.line_pattern(disc.D, disc.p)
+    nc, npe = disc.nc, disc.npe
+    e = 4
+    blk = A.reshape(disc.E, nc, npe, disc.E, nc, npe)[e, :, :, e]
+    for i in range(npe):
+        for j in range(npe):
+            ref = -0.3 * blk[:, i, :, j] + (np.eye(nc) if i == j else 0)
+            if j in pat[i]:
+                assert np.allclose(Ab[e, i, j], ref, atol=1e-14)
+            else:
+                assert not np.any(Ab[e, i, j])
+
+
+def test_ilu0_reproduces_matrix_on_pattern():
+    # ILU(0) is characterised by (L U)_ij = A_ij for every (i, j) in the pattern
+    rng = np.random.default_rng(1)
+    D, p, nc = 2, 3, 3
+    pat = S.line_pattern(D, p)
+    npe = (p + 1) ** D
+    Ab = np.zeros((1, npe, npe, nc, nc))
+    for i in range(npe):
+        for j in pat[i]:
+            Ab[0, i, j] = 0.1 * rng.standard_normal((nc, nc))
+        Ab[0, i, i] += 3 * np.eye(nc)
+    F = S.ilu0(Ab, pat)[0]
+    L = np.zeros((npe * nc, npe * nc))
+    Uu = np.zeros_like(L)
+    for i in range(npe):
+        for j in pat[i]:
+            blk = F[i, j]
+            if j < i:
+                L[i * nc:(i + 1) * nc, j * nc:(j + 1) * nc] = blk
+            else:
+                Uu[i * nc:(i + 1) * nc, j * nc:(j + 1) * nc] = blk
+        L[i * nc:(i + 1) * nc, i * nc:(i + 1) * nc] = np.eye(nc)
+    LU = (L @ Uu).reshape(npe, nc, npe, nc)
+    for i in range(npe):
+        for j in pat[i]:
+            assert np.allclose(LU[i, :, j, :], Ab[0, i, j], atol=1e-13)
+    # and the apply is the exact (LU)^-1
+    r = rng.standard_normal((1, nc, npe))
+    z = S.ilu_apply(S.ilu0(Ab, pat), pat, r)
+    zz = np.linalg.solve(L @ Uu, r[0].T.ravel()).reshape(npe, nc).T
+    assert np.allclose(z[0], zz, atol=1e-12)
+
+
+def test_ilu0_is_exact_lu_when_pattern_is_full():
+    # with p = 1 in 1-D-like blocks (D=2, p=1 gives 3 of 4 couplings; use a
+    # dense random block instead): ILU(0) on a full pattern equals LU
+    rng = np.random.default_rng(2)
+    n, nc = 5, 2
+    pat = [list(range(n)) for _ in range(n)]
+    Ab = 0.2 * rng.standard_normal((1, n, n, nc, nc))
+    for i in range(n):
+        Ab[0, i, i] += 2 * np.eye(nc)
+    F = S.ilu0(Ab, pat)
+    r = rng.standard_normal((1, nc, n))
+    z = S.ilu_apply(F, pat, r)
+    dense = Ab[0].transpose(0, 2, 1, 3).reshape(n * nc, n * nc)
+    assert np.allclose(z[0].T.ravel(), np.linalg.solve(dense, r[0].T.ravel()), atol=1e-12)
+
+
+def test_gmres_full_space_equals_direct_solve():
+    rng = np.random.default_rng(3)
+    n = 40
+    A = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / math.sqrt(n)
+    b = rng.standard_normal(n)
+    x, its, rel = S.gmres(lambda v: A @ v, b, tol=1e-14, restart=n)
+    assert np.allclose(x, np.linalg.solve(A, b), atol=1e-11)
+    P = np.linalg.inv(A + 0.05 * rng.standard_normal((n, n)))
+    x2, its2, _ = S.gmres(lambda v: A @ v, b, precond=lambda v: P @ v, tol=1e-12, restart=n)
+    assert np.allclose(x2, np.linalg.solve(A, b), atol=1e-10)
+    assert its2 < its
+
+
+def _vortex_small():
+    m = I.vortex_mesh(4, 2, perturb=0.1)
+    disc = Discretization(m, EULER)
+    return disc, I.vortex_state(m)
+
+
+def test_newton_bdf2_converges_quadratically_with_fresh_jacobian():
+    disc, U0 = _vortex_small()
+    F = lambda X: full_residual(disc, X)
+    jac = lambda X: (JAC.K11(disc, X), None, None)
+    pat = S.line_pattern(disc.D, disc.p)
+
+    def pc(K, shift, scale):
+        Fct = S.ilu0(S.masked_blocks(disc, K[0], shift, scale), pat)
+        return lambda v: S.ilu_apply(Fct, pat, v.reshape(U0.shape)).ravel()
+    U1, st = S.newton_bdf2(F, jac, U0, None, 0.2, first=True, rtol=1e-12, gmres_tol=1e-12,
+                           restart=200, reuse=1, precond_builder=pc)
+    h = np.array(st["hist"])
+    assert st["newton"] <= 5
+    # quadratic: each error roughly the square of the previous (relative)
+    rel = h / h[0]
+    assert rel[2] < 10 * rel[1] ** 2 + 1e-13
+    # the update solves the BDF1 stage equation
+    G = U1 - U0 - 0.2 * F(U1)
+    assert np.linalg.norm(G) <= 1e-12 * np.linalg.norm(0.2 * F(U0)) * 1.01
+
+
+def test_preconditioner_reduces_gmres_iterations():
+    # qualitative statement of Sec. 5.5: without the preconditioner many more
+    # GMRES iterations are needed for the same tolerance
+    disc, U0 = _vortex_small()
+    K = JAC.K11(disc, U0)
+    pat = S.line_pattern(disc.D, disc.p)
+    dt = 0.5
+    Fct = S.ilu0(S.masked_blocks(disc, K, 1.0, -dt), pat)
+    mv = lambda v: S.split_matvec(K, None, None, v, 1.0, -dt)
+    b = np.random.default_rng(4).standard_normal(U0.size)
+    _, it_p, _ = S.gmres(mv, b, lambda v: S.ilu_apply(Fct, pat, v.reshape(U0.shape)).ravel(),
+                         tol=1e-8, restart=300)
+    _, it_n, _ = S.gmres(mv, b, None, tol=1e-8, restart=300)
+    assert it_n > 2 * it_p
