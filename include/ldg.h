@@ -1,0 +1,289 @@
+/*
+ * ldg.h -- C ABI of the GB300 Line-DG library (libldg.so).
+ *
+ * Line-based discontinuous Galerkin discretisation of Persson, "A sparse and
+ * high-order accurate line-based discontinuous Galerkin method for
+ * unstructured meshes": residual evaluation, the line-sparse Jacobian, its
+ * split Jacobian-vector product, the element-block ILU(0) preconditioner and
+ * a BDF2 Newton-GMRES step.
+ *
+ * Conventions for every call
+ *   - returns LDG_OK (0) or a negative LDG_ERR_* code; on error nothing the
+ *     caller owns has been freed, and outputs may be partially written;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); work is enqueued on it and the call returns without waiting
+ *     unless stated otherwise;
+ *   - pointers named U, R, Q, x, y, r, z are DEVICE pointers owned by the
+ *     caller; the library never frees them;
+ *   - the library owns the handle and every object it returns (tables,
+ *     metrics, Jacobians, factors, Krylov bases) until the matching destroy
+ *     call;
+ *   - nodal arrays use the layout [n_elem][n_c][(p+1)^D] (row-major) with
+ *     local node a = i + (p+1) j + (p+1)^2 k, i running along reference
+ *     direction 1 (Sec. 2.1); the flat DOF index is (e n_c + c) (p+1)^D + a.
+ */
+#ifndef LDG_H
+#define LDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LDG_OK 0
+#define LDG_ERR_ARG (-1)              /* invalid argument or size           */
+#define LDG_ERR_CUDA (-2)             /* a CUDA runtime call failed         */
+#define LDG_ERR_MESH (-3)             /* non-conforming mesh, bad face
+                                         orientation, non-symmetric node set,
+                                         inconsistent switch, J <= 0       */
+#define LDG_ERR_NONFINITE (-4)        /* NaN/Inf in a residual or norm      */
+#define LDG_ERR_GMRES_BREAKDOWN (-5)  /* Krylov basis lost rank             */
+#define LDG_ERR_NEWTON_MAXIT (-6)     /* Newton iteration cap reached       */
+#define LDG_ERR_NOT_BUILT (-7)        /* object used before it was built    */
+#define LDG_ERR_UNSUPPORTED (-8)      /* (D, p, equation) not compiled in   */
+
+/* ---- equations (Sec. 2.1 Eq. 1, Sec. 3 Eq. 14, Sec. 5 Eqs. 42-48) ------- */
+#define LDG_EQ_POISSON 0        /* -div(grad u) = f, F = -q, n_c = 1         */
+#define LDG_EQ_EULER 1          /* compressible Euler, n_c = D + 2           */
+#define LDG_EQ_NAVIER_STOKES 2  /* compressible NS, constant mu, n_c = D + 2 */
+#define LDG_EQ_ADVECTION 3      /* scalar u_t + div(a u) = 0, n_c = 1        */
+
+#define LDG_FLUX_ROE 0  /* Roe averages, Harten entropy fix delta = 0.1 c   */
+#define LDG_FLUX_LF 1   /* local Lax-Friedrichs (Rusanov)                  */
+
+#define LDG_BC_DIRICHLET 0  /* Eqs. 27-28: u^ = g_D, penalty C11_b        */
+#define LDG_BC_WALL 1       /* no-slip adiabatic wall (NS; builder-defined) */
+
+#define LDG_PREC_FP32 0
+#define LDG_PREC_FP64 1
+
+/*
+ * Mesh (host memory, copied by ldg_setup). Sec. 2.1: each element carries
+ * a Cartesian grid of (p+1)^D nodes x_ijk = x(X_ijk), X_ijk = (s_i, s_j, s_k).
+ *   s        [p+1]                    increasing node set on [0,1], s_0 = 0,
+ *                                     s_p = 1, symmetric (s_{p-i} = 1 - s_i)
+ *   nodes    [n_elem][(p+1)^D][D]     node coordinates
+ *   vertices [n_elem][2^D]            global vertex ids; local corner c sits at
+ *                                     reference corner (c&1, (c>>1)&1, (c>>2)&1);
+ *                                     periodic images share ids
+ *   btag     [n_elem][2D]             face f = 2d + end (end 0: X_d = 0, end 1:
+ *                                     X_d = 1); -1 = interior (matched through
+ *                                     vertex ids), >= 0 = boundary tag
+ */
+typedef struct {
+  int32_t D;
+  int32_t p;
+  int64_t n_elem;
+  const double* s;
+  const double* nodes;
+  const int64_t* vertices;
+  const int32_t* btag;
+} ldg_mesh_t;
+
+/*
+ * Equations and fluxes (host memory, copied).
+ *   kind, flux        LDG_EQ_*, LDG_FLUX_*
+ *   gamma, mu, Pr     ideal gas ratio, constant viscosity, Prandtl number
+ *   C11, C11_b        LDG penalty at interior faces (0 = minimal dissipation)
+ *                     and at Dirichlet/wall boundaries (> 0), Eqs. 25, 27
+ *   adv[3]            advection velocity (LDG_EQ_ADVECTION)
+ *   n_bc, bc_kind     bc_kind[tag] = LDG_BC_* for boundary tags 0..n_bc-1
+ *   g_D               [n_elem][n_c][(p+1)^D] Dirichlet data (read at boundary
+ *                     face nodes) or NULL
+ *   source            [n_elem][n_c][(p+1)^D] source S(x) added to R, or NULL
+ */
+typedef struct {
+  int32_t kind;
+  int32_t flux;
+  double gamma;
+  double mu;
+  double Pr;
+  double C11;
+  double C11_b;
+  double adv[3];
+  int32_t n_bc;
+  const int32_t* bc_kind;
+  const double* g_D;
+  const double* source;
+} ldg_equations_t;
+
+typedef struct ldg_handle ldg_handle_t;
+typedef struct ldg_jac ldg_jac_t;
+typedef struct ldg_pc ldg_pc_t;
+
+/*
+ * Build a handle: 1-D rules (Gauss-Legendre with ceil((3p+1)/2) points,
+ * Lagrange basis, mass matrix, Cholesky, Sec. 2.2), face matching and
+ * neighbour-node tables (Sec. 2.1), the switch function (Sec. 3) and the
+ * metric terms J, n_d at Gauss points and n^+- at line ends (Eqs. 2, 4-6,
+ * Sec. 2.2), uploaded to the current device. Synchronous. *out receives the
+ * handle (freed by ldg_destroy).
+ * Errors: LDG_ERR_ARG (sizes), LDG_ERR_MESH, LDG_ERR_UNSUPPORTED, LDG_ERR_CUDA.
+ */
+int ldg_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_handle_t** out);
+
+/*
+ * The host half of ldg_setup alone, for checks without a GPU: writes the
+ * integer tables and metric terms the device would receive to any non-NULL
+ * host buffer (sizes as for ldg_export_tables, plus ng [n_elem][D][nl][n_q][D],
+ * nend [n_elem][D][nl][2][D] (n^- at end 0, n^+ at end 1), invJ
+ * [n_elem][(p+1)^D], and tables = Phi [n_q][p+1], Kd [p+1][n_q], L0 [p+1],
+ * L1 [p+1] of Sec. 2.2). Touches no device. Errors as ldg_setup.
+ */
+int ldg_setup_host(const ldg_mesh_t* mesh, const ldg_equations_t* eq, int64_t* nbr, int8_t* sw,
+                   double* ng, double* nend, double* invJ, double* tables);
+
+/* Free the handle and everything it owns. NULL is accepted. */
+int ldg_destroy(ldg_handle_t* h);
+
+/*
+ * Sizes: info[0..9] = {D, p, n_c, n_elem, (p+1)^D, (p+1)^(D-1) lines per
+ * direction, n_q Gauss points, ndof, K11 floats, K12 floats}.
+ */
+int ldg_info(const ldg_handle_t* h, int64_t info[10]);
+
+/*
+ * Copy the integer tables to host memory (for bit-exact checks):
+ *   nbr [n_elem][D][(p+1)^(D-1)][2]  global id e (p+1)^D + a of the outside
+ *                                    node of each line end, or -1 - tag
+ *   sw  [n_elem][D][2]               switch S^-_d (end 0), S^+_d (end 1)
+ * Either pointer may be NULL.
+ */
+int ldg_export_tables(const ldg_handle_t* h, int64_t* nbr, int8_t* sw);
+
+/*
+ * Residual of the semi-discrete system, dU/dt = R(U) (Eqs. 10, 31, 36):
+ * R = -(1/J) sum_d r^(d) + S, r^(d) from Eq. 7 per line. For second-order
+ * equations the LDG gradient Q = D(U) (Eqs. 19-20, 32) is evaluated first
+ * into a library-owned buffer. FP64 throughout. U, R: device [n_elem][n_c][(p+1)^D].
+ */
+int ldg_residual(ldg_handle_t* h, const double* U, double* R, void* stream);
+
+/* The LDG gradient alone: Q = D(U), device [n_elem][n_c][D][(p+1)^D], FP64. */
+int ldg_gradient(ldg_handle_t* h, const double* U, double* Q, void* stream);
+
+/* R(U, Q) for a given Q (the split form of Eq. 33), FP64. */
+int ldg_residual_uq(ldg_handle_t* h, const double* U, const double* Q, double* R, void* stream);
+
+/*
+ * Jacobian matrices in the line-block format (Sec. 4.1 Eq. 35, Sec. 2.3):
+ * K11 = dR/dU and, for second-order equations, K12 = dR/dQ and the constant
+ * K21 = dD/dU. If *J is NULL a new object is allocated, otherwise its
+ * buffers are reused. prec = LDG_PREC_FP32 (values computed in FP32 from the
+ * FP64 state) or LDG_PREC_FP64. Storage, per element e, direction d, line l,
+ * with L = (e D + d) nl + l and NL = n_elem D nl lines:
+ *   K11 in-line : K11[((i (p+1) + j) n_c + c) n_c + c'][L]   dR_(i,c)/dU_(j,c')
+ *   K11 faces   : K11[OFF + ((end (p+1) + i) n_c + c) n_c + c'][L]
+ *                 dR_(i,c)/dU_out(end,c'),  OFF = (p+1)^2 n_c^2
+ *   K12         : same with n_c x (n_c D) blocks, index c' -> c' D + b,
+ *                 one face block per line (the end whose switch takes the
+ *                 viscous flux from outside), end index dropped
+ *   K21         : scalar, in-line [(i (p+1) + j) D + b][L], face
+ *                 [KOFF + i D + b][L] for the end whose u^ comes from outside
+ * (entry-major, line-minor: a thread per line reads coalesced).
+ */
+int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_t** J, void* stream);
+
+/* Free a Jacobian object. NULL is accepted. */
+int ldg_jac_destroy(ldg_jac_t* J);
+
+/*
+ * Copy the Jacobian arrays to host memory in the layout above (FP32 or FP64
+ * as built). Any pointer may be NULL. Synchronous.
+ */
+int ldg_jac_export(const ldg_jac_t* J, void* K11, void* K12, void* K21);
+
+/*
+ * Split Jacobian-vector product (Eq. 41):
+ *   y = shift x + scale (K11 x + K12 (K21 x)).
+ * With shift = 1, scale = -alpha dt this is the Newton matrix of Eq. 39.
+ * x, y: device [ndof] of type float (prec = LDG_PREC_FP32) or double
+ * (LDG_PREC_FP64; matrix values are used at the precision they were built).
+ */
+int ldg_jacvec(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, const void* x,
+               void* y, int prec, void* stream);
+
+/*
+ * Block-Jacobi preconditioner (Sec. 4.2): per element, A~_e = shift I +
+ * scale mask(K11 + K12 K21) on the element-local Line-DG pattern (node i
+ * couples to the Dp+1 nodes of its D lines), inter-element couplings and
+ * out-of-pattern fill dropped, then block ILU(0) in that pattern with n_c x
+ * n_c blocks in node order i + (p+1) j + (p+1)^2 k. Factors are kept at
+ * the Jacobian's precision. *P allocated if NULL, else reused.
+ */
+int ldg_precond(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, ldg_pc_t** P,
+                void* stream);
+
+/* z = (L U)^{-1} r per element; r, z device [ndof] float or double (prec). */
+int ldg_precond_apply(ldg_handle_t* h, const ldg_pc_t* P, const void* r, void* z, int prec,
+                      void* stream);
+
+/* Free a preconditioner. NULL is accepted. */
+int ldg_pc_destroy(ldg_pc_t* P);
+
+/*
+ * Copy the ILU(0) factors to host: [n_elem][(p+1)^D][Dp+1][n_c][n_c] in the
+ * precision they were built; column order of each row = sorted local node
+ * ids of its pattern. Strictly-lower blocks hold L (unit diagonal implied),
+ * the rest hold U. Synchronous.
+ */
+int ldg_pc_export(const ldg_pc_t* P, void* factors);
+
+/* ---- implicit step ----------------------------------------------------- */
+#define LDG_MODE_FP64 0   /* FP64 Jacobian, ILU, Krylov basis              */
+#define LDG_MODE_MIXED 1  /* FP32 Jacobian/ILU/Krylov, FP64 refinement      */
+
+#define LDG_PRED_EXTRAP 0  /* U0 = 2 U^n - U^{n-1} (U^n on the first step)   */
+#define LDG_PRED_GIVEN 1   /* U0 = the caller's U_next on entry             */
+
+typedef struct {
+  int32_t mode;          /* LDG_MODE_*                                        */
+  int32_t predictor;     /* LDG_PRED_*                                        */
+  int32_t first_step;    /* 1: BDF1 (U_nm1 unused)                            */
+  int32_t restart;       /* GMRES restart length (<= 64)                      */
+  int32_t max_newton;    /* iteration cap                                      */
+  int32_t reuse;         /* rebuild K, P when Newton its since rebuild > reuse */
+  int32_t max_refine;    /* FP64 iterative-refinement sweeps per linear solve */
+  int32_t force_rebuild; /* 1: build K, P at the first Newton iteration       */
+  double rtol;           /* ||G(U)||_2 <= rtol ||G(U^n)||_2                  */
+  double gmres_tol;      /* relative tolerance of each linear solve           */
+} ldg_solver_opts_t;
+
+typedef struct {
+  int32_t newton_its;
+  int32_t gmres_its;
+  int32_t jac_builds;
+  int32_t refine_sweeps;
+  double res0;           /* ||G(U^n)||_2                                      */
+  double res_final;      /* ||G(U_next)||_2                                   */
+  double res_pred;       /* ||G(U0)||_2 of the predictor                      */
+  double t_residual_ms;  /* host-timed phases (events)                        */
+  double t_jacobian_ms;
+  double t_precond_ms;
+  double t_linear_ms;
+} ldg_step_stats_t;
+
+/*
+ * One BDF2 time level (BDF1 when opts->first_step) solved by Newton's
+ * method on G(U) = U - 4/3 U^n + 1/3 U^{n-1} - 2/3 dt R(U) with
+ * (I - 2/3 dt A) delta = -G(U) (Eqs. 39-41) by right-preconditioned
+ * GMRES(restart) with the block-Jacobi ILU(0) preconditioner, Jacobian
+ * re-use (Sec. 4.3), and in LDG_MODE_MIXED FP64 iterative refinement of each
+ * linear solve. U_next: device FP64 [ndof], in/out. U_nm2 is accepted for
+ * interface symmetry and may be NULL. Synchronises on stream (reads norms).
+ * Errors: LDG_ERR_NEWTON_MAXIT, LDG_ERR_NONFINITE, LDG_ERR_GMRES_BREAKDOWN.
+ */
+int ldg_newton_step(ldg_handle_t* h, double* U_next, const double* U_n, const double* U_nm1,
+                    const double* U_nm2, double dt, const ldg_solver_opts_t* opts,
+                    ldg_step_stats_t* stats, void* stream);
+
+/* ||x||_2 of a device FP64 vector (synchronous; for drivers and tests). */
+int ldg_norm2(ldg_handle_t* h, const double* x, int64_t n, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDG_H */

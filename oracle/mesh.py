@@ -211,10 +211,25 @@ def switches(mesh, conn):
 # metric terms
 # ---------------------------------------------------------------------------
 def _cofactor(G):
-    """J G^{-T} for G[..., a, b] = dx_a/dX_b, via det and inverse."""
-    J = np.linalg.det(G)
-    Ginv = np.linalg.inv(G)
-    return J, J[..., None, None] * np.swapaxes(Ginv, -1, -2)
+    """det G and J G^{-T} (the cofactor matrix) for G[..., a, b] = dx_a/dX_b,
+    written out for 2x2 and 3x3 (works in any float precision)."""
+    D = G.shape[-1]
+    C = np.zeros_like(G)
+    if D == 2:
+        C[..., 0, 0] = G[..., 1, 1]
+        C[..., 0, 1] = -G[..., 1, 0]
+        C[..., 1, 0] = -G[..., 0, 1]
+        C[..., 1, 1] = G[..., 0, 0]
+        J = G[..., 0, 0] * G[..., 1, 1] - G[..., 0, 1] * G[..., 1, 0]
+    else:
+        for a in range(3):
+            for b in range(3):
+                a1, a2 = [r for r in range(3) if r != a]
+                b1, b2 = [c for c in range(3) if c != b]
+                minor = G[..., a1, b1] * G[..., a2, b2] - G[..., a1, b2] * G[..., a2, b1]
+                C[..., a, b] = minor if (a + b) % 2 == 0 else -minor
+        J = sum(G[..., 0, b] * C[..., 0, b] for b in range(3))
+    return J, C
 
 
 class Metrics:
@@ -223,36 +238,42 @@ class Metrics:
     nplus[d], nminus[d] : [E, nl, D]."""
 
     def __init__(self, mesh, rules):
+        # The metric terms are formed in extended precision and rounded to
+        # float64 once: the residual subtracts flux values of size |F| |n|
+        # from each other, so independent float64 roundings of n (node
+        # coordinates of size L, spacings h) would show up in R amplified by
+        # about (L / h) |F| / |R|.
         D, p = mesh["D"], mesh["p"]
-        X = mesh["nodes"]                          # [E, npe, D]
+        X = mesh["nodes"].astype(np.longdouble)    # [E, npe, D]
         E = X.shape[0]
         # G at the nodes: dx_a/dX_b by the nodal derivative matrix along b
-        Gn = np.zeros((E, (p + 1) ** D, D, D))
+        Gn = np.zeros((E, (p + 1) ** D, D, D), dtype=np.longdouble)
         for b in range(D):
             for a in range(D):
                 xl = to_lines(X[..., a], D, p, b)    # [E, nl, p+1]
-                dl = np.einsum("ij,elj->eli", rules.Dn, xl)
+                dl = np.einsum("ij,elj->eli", rules.Dn_x, xl)
                 Gn[:, :, a, b] = from_lines(dl, D, p, b)
-        self.J, cof_n = _cofactor(Gn)
-        if np.any(self.J <= 0):
+        J, cof_n = _cofactor(Gn)
+        if np.any(J <= 0):
             raise MeshError("non-positive mapping Jacobian at a node")
+        self.J = J.astype(np.float64)
         self.ng, self.nplus, self.nminus = [], [], []
         for d in range(D):
             # G at (xi_q along d, nodes in the other directions)
-            Gq = np.zeros((E, (p + 1) ** (D - 1), rules.nq, D, D))
+            Gq = np.zeros((E, (p + 1) ** (D - 1), rules.nq, D, D), dtype=np.longdouble)
             for a in range(D):
                 xl = to_lines(X[..., a], D, p, d)
-                Gq[..., a, d] = np.einsum("qj,elj->elq", rules.dPhi, xl)
+                Gq[..., a, d] = np.einsum("qj,elj->elq", rules.dPhi_x, xl)
                 for b in range(D):
                     if b == d:
                         continue
                     gl = to_lines(Gn[:, :, a, b], D, p, d)
-                    Gq[..., a, b] = np.einsum("qj,elj->elq", rules.Phi, gl)
+                    Gq[..., a, b] = np.einsum("qj,elj->elq", rules.Phi_x, gl)
             _, cof_q = _cofactor(Gq)
-            self.ng.append(cof_q[..., :, d])                       # [E, nl, nq, D]
+            self.ng.append(cof_q[..., :, d].astype(np.float64))     # [E, nl, nq, D]
             cl = np.stack([to_lines(cof_n[:, :, a, d], D, p, d) for a in range(D)], axis=-1)
-            self.nplus.append(cl[:, :, p, :])                        # N_d^+ at xi = 1
-            self.nminus.append(-cl[:, :, 0, :])                      # N_d^- at xi = 0
+            self.nplus.append(cl[:, :, p, :].astype(np.float64))     # N_d^+ at xi = 1
+            self.nminus.append((-cl[:, :, 0, :]).astype(np.float64))  # N_d^- at xi = 0
 
 
 def pattern_counts(mesh, conn):

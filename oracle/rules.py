@@ -17,11 +17,11 @@ def n_gauss(p: int) -> int:
     return (3 * p + 2) // 2
 
 
-def gauss_legendre_01(nq: int):
+def gauss_legendre_01(nq: int, dtype=np.float64):
     """Gauss-Legendre points/weights on [0,1], by Newton's method on P_nq
-    evaluated with the three-term Legendre recurrence."""
-    k = np.arange(1, nq + 1)
-    x = np.cos(math.pi * (k - 0.25) / (nq + 0.5))
+    evaluated with the three-term Legendre recurrence (in `dtype`)."""
+    k = np.arange(1, nq + 1, dtype=dtype)
+    x = np.cos(dtype(np.pi) * (k - dtype(0.25)) / (nq + dtype(0.5)))
     for _ in range(100):
         p0 = np.ones_like(x)
         p1 = x.copy()
@@ -30,8 +30,15 @@ def gauss_legendre_01(nq: int):
         dp = nq * (x * p1 - p0) / (x * x - 1.0)
         dx = p1 / dp
         x = x - dx
-        if np.max(np.abs(dx)) < 1e-16:
+        if np.max(np.abs(dx)) < 16 * np.finfo(dtype).eps:
             break
+    for _ in range(3):   # polish at the working precision
+        p0 = np.ones_like(x)
+        p1 = x.copy()
+        for m in range(2, nq + 1):
+            p0, p1 = p1, ((2 * m - 1) * x * p1 - (m - 1) * p0) / m
+        dp = nq * (x * p1 - p0) / (x * x - 1.0)
+        x = x - p1 / dp
     p0 = np.ones_like(x)
     p1 = x.copy()
     for m in range(2, nq + 1):
@@ -42,14 +49,14 @@ def gauss_legendre_01(nq: int):
     return 0.5 * (x[order] + 1.0), 0.5 * w[order]
 
 
-def lagrange(s, x):
+def lagrange(s, x, dtype=np.float64):
     """phi_i(x_q) and phi_i'(x_q) for the nodal basis phi_i(s_j) = delta_ij,
     written out as products (returns arrays [len(x), len(s)])."""
-    s = np.asarray(s, dtype=np.float64)
-    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    s = np.asarray(s, dtype=dtype)
+    x = np.atleast_1d(np.asarray(x, dtype=dtype))
     n = len(s)
-    phi = np.ones((len(x), n))
-    dphi = np.zeros((len(x), n))
+    phi = np.ones((len(x), n), dtype=dtype)
+    dphi = np.zeros((len(x), n), dtype=dtype)
     for i in range(n):
         for j in range(n):
             if j != i:
@@ -57,7 +64,7 @@ def lagrange(s, x):
         for k in range(n):
             if k == i:
                 continue
-            term = np.full(len(x), 1.0 / (s[i] - s[k]))
+            term = np.full(len(x), 1 / (s[i] - s[k]), dtype=dtype)
             for j in range(n):
                 if j != i and j != k:
                     term *= (x - s[j]) / (s[i] - s[j])
@@ -87,6 +94,11 @@ class Rules:
         self.chol = np.linalg.cholesky(self.M)
         _, self.Dn = lagrange(self.s, self.s)
         self.wnod = self.Phi.T @ self.wq
+        # extended-precision copies for the metric terms (rounded once)
+        X = np.longdouble
+        xq_x, _ = gauss_legendre_01(self.nq, X)
+        self.Phi_x, self.dPhi_x = lagrange(self.s, xq_x, X)
+        _, self.Dn_x = lagrange(self.s, self.s, X)
 
     def mass_solve(self, b):
         """Solve M r = b along the last axis of b with the Cholesky factor

@@ -1,0 +1,96 @@
+// C-ABI entry points for the residual path and small device utilities.
+#include <cmath>
+
+#include "ldg_internal.h"
+
+namespace ldg {
+cudaError_t residual_2d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
+cudaError_t residual_3d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
+cudaError_t gradient_2d(const ldg_handle* h, const double* U, double* Q, cudaStream_t st);
+cudaError_t gradient_3d(const ldg_handle* h, const double* U, double* Q, cudaStream_t st);
+
+bool residual_supported(int D, int p, int kind) {
+  if (p < 1 || p > 4) return false;
+  if (D == 2) return kind >= 0 && kind <= 3;
+  if (D == 3) return kind >= 0 && kind <= 2;
+  return false;
+}
+
+cudaError_t launch_gradient(const ldg_handle* h, const double* U, double* Q, cudaStream_t st) {
+  return h->D == 2 ? gradient_2d(h, U, Q, st) : gradient_3d(h, U, Q, st);
+}
+
+cudaError_t launch_residual(const ldg_handle* h, const double* U, const double* Q, double* R,
+                            cudaStream_t st) {
+  return h->D == 2 ? residual_2d(h, U, Q, R, st) : residual_3d(h, U, Q, R, st);
+}
+
+// sum of squares, one partial per block, finished by a single block
+__global__ void k_sumsq(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(x[i], x[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[0] = s;
+  }
+}
+
+}  // namespace ldg
+
+using namespace ldg;
+
+extern "C" int ldg_gradient(ldg_handle_t* h, const double* U, double* Q, void* stream) {
+  if (!h || !U || !Q) return LDG_ERR_ARG;
+  if (!h->viscous()) return LDG_ERR_UNSUPPORTED;
+  return launch_gradient(h, U, Q, (cudaStream_t)stream) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_residual_uq(ldg_handle_t* h, const double* U, const double* Q, double* R,
+                               void* stream) {
+  if (!h || !U || !R || (h->viscous() && !Q)) return LDG_ERR_ARG;
+  return launch_residual(h, U, Q, R, (cudaStream_t)stream) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_residual(ldg_handle_t* h, const double* U, double* R, void* stream) {
+  if (!h || !U || !R) return LDG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->viscous() && launch_gradient(h, U, h->Qbuf, st) != cudaSuccess) return LDG_ERR_CUDA;
+  return launch_residual(h, U, h->viscous() ? h->Qbuf : nullptr, R, st) == cudaSuccess
+             ? LDG_OK
+             : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_norm2(ldg_handle_t* h, const double* x, int64_t n, double* out, void* stream) {
+  if (!h || !x || !out || n < 0) return LDG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = 1024;
+  k_sumsq<<<blocks, 256, 0, st>>>(x, n, h->red);
+  k_sum_parts<<<1, 1024, 0, st>>>(h->red, blocks, h->red + blocks);
+  double s = 0.0;
+  LDG_CUDA_TRY(cudaMemcpyAsync(&s, h->red + blocks, sizeof(double), cudaMemcpyDeviceToHost, st));
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(s)) return LDG_ERR_NONFINITE;
+  *out = std::sqrt(s);
+  return LDG_OK;
+}

@@ -1,0 +1,176 @@
+"""GPU parity of the FP64 LDG gradient and residual against the oracle,
+element by element, through the C ABI. Tolerance: 1e-12 relative to
+max|R_oracle| on non-equilibrium seeded states.
+
+The reference is the oracle evaluated in extended precision (np.longdouble
+inputs through the same code): the residual cancels flux values that are
+about p^2 |F| / (h |R|) times larger than R, so at the 64x64 workload
+resolution the float64 oracle's own rounding is already 1.0e-12 relative
+to an extended-precision evaluation and cannot resolve a 1e-12 bound."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1204_1533_gb300 import inputs as I
+from oracle.residual import Discretization, full_residual, gradient
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+EULER = {"kind": "euler", "gamma": 1.4, "flux": "roe"}
+
+
+def ns(mu=0.01):
+    return {"kind": "ns", "gamma": 1.4, "flux": "roe", "mu": mu, "Pr": 0.72}
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1204_1533_gb300 import build, ldg
+    build.build()
+    return ldg
+
+
+def _free_stream(m, nc, rho=1.0, v=(0.8, -0.3, 0.2), p=2.5):
+    D = m["D"]
+    E, npe = m["nodes"].shape[:2]
+    U = np.zeros((E, nc, npe))
+    U[:, 0] = rho
+    for a in range(D):
+        U[:, 1 + a] = rho * v[a]
+    U[:, D + 1] = p / 0.4 + 0.5 * rho * sum(x * x for x in v[:D])
+    return U
+
+
+def _case(name):
+    if name == "euler2d_p4":
+        m = I.reorient(I.vortex_mesh(5, 4, perturb=0.15))[0]
+        return m, EULER, I.smooth_perturbation(m, I.vortex_state(m), 0.05, periods=[10, 10])
+    if name == "lf2d_p3":
+        m = I.vortex_mesh(5, 3, perturb=0.15)
+        return m, dict(EULER, flux="lf"), I.smooth_perturbation(m, I.vortex_state(m), 0.05)
+    if name == "euler3d_p2":
+        m = I.reorient(I.structured_mesh((3, 3, 3), 2, (0,) * 3, (1,) * 3, (True,) * 3, perturb=0.1))[0]
+        return m, EULER, I.smooth_perturbation(m, _free_stream(m, 5), 0.05, periods=[1, 1, 1])
+    if name == "ns3d_tgv_p3":
+        m = I.tgv_mesh(4, 3)
+        return m, ns(1 / 1600), I.smooth_perturbation(m, I.tgv_state(m), 0.05)
+    if name == "ns3d_p4":
+        m = I.structured_mesh((3, 3, 3), 4, (0,) * 3, (2 * math.pi,) * 3, (True,) * 3, perturb=0.1)
+        return m, ns(0.05), I.smooth_perturbation(m, I.tgv_state(m, mach=0.3), 0.05)
+    if name == "ns2d_p2_reoriented":
+        m = I.reorient(I.vortex_mesh(4, 2, perturb=0.15))[0]
+        return m, ns(0.05), I.smooth_perturbation(m, I.vortex_state(m), 0.05, periods=[10, 10])
+    if name == "ns3d_p1":
+        m = I.reorient(I.structured_mesh((3, 3, 3), 1, (0,) * 3, (1,) * 3, (True,) * 3, perturb=0.1))[0]
+        return m, ns(0.02), I.smooth_perturbation(m, _free_stream(m, 5), 0.1, periods=[1, 1, 1])
+    if name == "poisson_p3":
+        m = I.poisson_square_mesh(8, 3)
+        eq = {"kind": "poisson", "C11b": 1.0, "bc": {0: "dirichlet"},
+              "gD": np.zeros((m["nodes"].shape[0], 1, 16)), "source": I.poisson_source(m)}
+        return m, eq, I.poisson_exact(m) * 1.1 + 0.05 * I.random_state((64, 1, 16))
+    if name == "advection_p3":
+        m = I.reorient(I.poisson_square_mesh(5, 3, perturb=0.2))[0]
+        x, y = m["nodes"][..., 0], m["nodes"][..., 1]
+        g = np.sin(3 * x + y)[:, None]
+        eq = {"kind": "advection", "adv": [0.7, -0.4], "bc": {0: "dirichlet"}, "gD": g}
+        return m, eq, g + 0.1 * np.cos(5 * y)[:, None]
+    if name == "channel_walls_p2":
+        m = I.channel_mesh(4, 4, 3, 2)
+        eq = dict(ns(0.01), bc={1: "wall"}, source=None)
+        return m, eq, I.channel_state(m)
+    if name == "single_element_poisson":
+        m = I.poisson_square_mesh(1, 4)
+        eq = {"kind": "poisson", "bc": {0: "dirichlet"}, "gD": np.zeros((1, 1, 25)),
+              "source": np.ones((1, 1, 25))}
+        return m, eq, I.random_state((1, 1, 25))
+    raise KeyError(name)
+
+
+CASES = ["euler2d_p4", "lf2d_p3", "euler3d_p2", "ns3d_tgv_p3", "ns3d_p4", "ns2d_p2_reoriented",
+         "ns3d_p1", "poisson_p3", "advection_p3", "channel_walls_p2", "single_element_poisson"]
+
+
+def _ext(a):
+    return None if a is None else np.asarray(a, dtype=np.longdouble)
+
+
+def _ref_residual(disc, U, gD=None, src=None):
+    return full_residual(disc, _ext(U), _ext(gD), _ext(src)).astype(np.float64)
+
+
+def _oracle_eq(eq):
+    out = dict(eq)
+    out.pop("gD", None)
+    out.pop("source", None)
+    out.setdefault("bc", {0: "dirichlet"})
+    return out
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_residual_matches_oracle(L, name):
+    import torch
+    m, eq, U = _case(name)
+    disc = Discretization(m, _oracle_eq(eq))
+    Ro = _ref_residual(disc, U, eq.get("gD"), eq.get("source"))
+    h = L.ldg_setup(m, eq)
+    Ut = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    R = torch.full_like(Ut, float("nan"))
+    L.ldg_residual(h, Ut, R)
+    torch.cuda.synchronize()
+    Rg = R.cpu().numpy()
+    assert np.all(np.isfinite(Rg))
+    err = np.abs(Rg - Ro).max()
+    assert err <= RTOL * np.abs(Ro).max(), (name, err, np.abs(Ro).max())
+
+
+@pytest.mark.parametrize("name", ["ns3d_tgv_p3", "ns2d_p2_reoriented", "poisson_p3", "channel_walls_p2"])
+def test_gradient_matches_oracle(L, name):
+    import torch
+    m, eq, U = _case(name)
+    disc = Discretization(m, _oracle_eq(eq))
+    Qo = gradient(disc, _ext(U), _ext(eq.get("gD"))).astype(np.float64)
+    h = L.ldg_setup(m, eq)
+    Ut = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    Q = torch.empty((h.E, h.nc, h.D, h.npe), dtype=torch.float64, device="cuda")
+    L.ldg_gradient(h, Ut, Q)
+    torch.cuda.synchronize()
+    # Q is a discrete derivative: its rounding scales with |U| / h, not with
+    # |Q| (rho E ~ 180 against grad(rho E) ~ 5 at Mach 0.1), so the bound is
+    # relative to max|Q| + max|U| / h_min per component
+    X = m["nodes"]
+    h_min = min(np.ptp(X[e, :, 0]) for e in range(X.shape[0]))
+    for c in range(h.nc):
+        scale = np.abs(Qo[:, c]).max() + np.abs(U[:, c]).max() / h_min
+        assert np.abs(Q.cpu().numpy()[:, c] - Qo[:, c]).max() <= RTOL * scale, c
+
+
+def test_free_stream_and_conservation_on_gpu(L):
+    import torch
+    from oracle.residual import conservation_weights
+    m = I.reorient(I.vortex_mesh(6, 4, perturb=0.15))[0]
+    h = L.ldg_setup(m, EULER)
+    U = torch.from_numpy(_free_stream(m, 4)).cuda()
+    R = torch.empty_like(U)
+    L.ldg_residual(h, U, R)
+    assert R.abs().max().item() < 1e-11
+    U2 = torch.from_numpy(I.smooth_perturbation(m, I.vortex_state(m), 0.05, periods=[10, 10])).cuda()
+    L.ldg_residual(h, U2, R)
+    W = torch.from_numpy(conservation_weights(Discretization(m, EULER))).cuda()[:, None, :]
+    tot = (W * R).sum(dim=(0, 2)).abs().max().item()
+    assert tot < 1e-13 * (W * R.abs()).sum().item()
+
+
+def test_full_size_vortex_64x64_p4(L):
+    """The 64x64, p=4 vortex workload at full size, every output checked."""
+    import torch
+    m = I.vortex_mesh(64, 4)
+    U = I.smooth_perturbation(m, I.vortex_state(m), 0.05)
+    Ro = _ref_residual(Discretization(m, EULER), U)
+    h = L.ldg_setup(m, EULER)
+    Ut = torch.from_numpy(U).cuda()
+    R = torch.empty_like(Ut)
+    L.ldg_residual(h, Ut, R)
+    torch.cuda.synchronize()
+    assert np.abs(R.cpu().numpy() - Ro).max() <= RTOL * np.abs(Ro).max()
