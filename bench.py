@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the Line-DG hot path on GB300.
+
+One step = one implicit BDF2 time level of the 2-D isentropic-vortex
+workload (64 x 64 perturbed periodic quads on [0,10]^2, p = 4, Euler with
+Roe flux, dt = 0.05) solved by Newton-GMRES(30) with the element-block
+ILU(0) preconditioner to ||G|| <= 1e-8 ||G(U^n)||, with the Jacobian and
+preconditioner rebuilt every step: every stage of the hot path (residual,
+Jacobian assembly, preconditioner build, split matvec, ILU apply, GMRES
+orthogonalisation, Newton update) runs in each step. The workload's stated
+precision is FP64; the mixed-precision step (FP32 Jacobian/ILU/Krylov,
+FP64 residual/update/refinement) is timed on the same data beside it.
+
+value = DOF advanced per second over the whole job (all ranks).
+`--impl reference` times the CPU oracle (the only other implementation of
+the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "residual+Jacobian DOF/s; implicit-step time mixed+learned vs FP64 @1e-8 res"
+WORKLOAD = "euler2d_vortex_64x64_p4_bdf2_dt0.05_newton_gmres30_ilu0"
+EQ = {"kind": "euler", "gamma": 1.4, "flux": "roe"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (non-tensor and tensor), TFLOP/s
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch (documented in the design doc)
+# ---------------------------------------------------------------------------
+def euler_residual_flops(D, p, nc, E):
+    """FP64 operations of one first-order residual (divisions and square
+    roots counted as one): per line interpolation, Gauss-point flux,
+    contraction with M^-1 dPhi^T W, two Roe fluxes and their lifting."""
+    N, NQ, NL = p + 1, (3 * p + 2) // 2, (p + 1) ** (D - 1)
+    f_e = 7 * D + 7
+    f_roe = 45 * D + 80
+    per_line = NQ * nc * (2 * N - 1) + NQ * f_e + NQ * N * nc * 2 + 2 * (f_roe + N * nc * 2)
+    return E * (D * NL * per_line + (p + 1) ** D * nc * (D + 1))
+
+
+def jac_bytes(h, esz):
+    """Compulsory HBM bytes of one Jacobian assembly: the K11 (+K12) values
+    written plus the state read."""
+    return h.ntiles * 32 * (h.nk11 + h.nk12) * esz + h.ndof * 8
+
+
+def jacvec_bytes(h, esz, vsz):
+    """One split matvec: matrix values read once, x read, y written."""
+    return h.ntiles * 32 * (h.nk11 + h.nk12) * esz + 2 * h.ndof * vsz
+
+
+def apply_bytes(h, esz, vsz):
+    """ILU(0) apply: factors + inverted diagonal blocks read, r read, z written."""
+    W = h.D * h.p + 1
+    return h.E * h.npe * (W + 1) * h.nc * h.nc * esz + 2 * h.ndof * vsz
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        from paper_1204_1533_gb300 import build
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_1204_1533_gb300 import inputs as I
+    from paper_1204_1533_gb300 import ldg
+
+    m = I.vortex_mesh(args.n, args.p)
+    U0 = I.vortex_state(m)
+    h = ldg.ldg_setup(m, EQ)
+    st = torch.cuda.current_stream()
+    dt = 0.05
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def run(mode, K, W, e2e=False):
+        """W warm-up + K timed BDF2 levels; returns per-step ms and stats."""
+        Un = torch.from_numpy(U0).cuda()
+        U1 = torch.empty_like(Un)
+        ldg.ldg_newton_step(h, U1, Un, None, None, dt, ldg.solver_opts(mode=mode, first_step=True))
+        Unm1, Un = Un, U1
+        hostbuf = None
+        if e2e:
+            hostbuf = [torch.empty(h.ndof, dtype=torch.float64).pin_memory() for _ in range(3)]
+            hostbuf[0].copy_(Un.view(-1).cpu())
+            hostbuf[1].copy_(Unm1.view(-1).cpu())
+        times, stats = [], []
+        for it in range(W + K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            Unext = torch.empty_like(Un)
+            e0.record(st)
+            if e2e:
+                Un_d = torch.empty_like(Un)
+                Unm1_d = torch.empty_like(Un)
+                Un_d.view(-1).copy_(hostbuf[0], non_blocking=True)
+                Unm1_d.view(-1).copy_(hostbuf[1], non_blocking=True)
+                s = ldg.ldg_newton_step(h, Unext, Un_d, Unm1_d, None, dt,
+                                        ldg.solver_opts(mode=mode, force_rebuild=True))
+                hostbuf[2].copy_(Unext.view(-1), non_blocking=True)
+            else:
+                s = ldg.ldg_newton_step(h, Unext, Un, Unm1, None, dt,
+                                        ldg.solver_opts(mode=mode, force_rebuild=True))
+            e1.record(st)
+            e1.synchronize()
+            if it >= W:
+                times.append(e0.elapsed_time(e1))
+                stats.append(s)
+            if e2e:
+                hostbuf[0], hostbuf[1], hostbuf[2] = hostbuf[2], hostbuf[0], hostbuf[1]
+            else:
+                Unm1, Un = Un, Unext
+        return times, stats
+
+    def kernel_ms(fn, reps=20):
+        for _ in range(3):
+            fn()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    # ---- timed FP64 steps (the workload's precision) ----------------------
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    l0 = ldg.ldg_launch_count()
+    t64, s64 = run(ldg.MODE_FP64, args.steps, args.warmup)
+    launches = (ldg.ldg_launch_count() - l0)
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    ms = float(np.mean(t64))
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    launches_per_step = launches / (args.steps + args.warmup + 1)
+    value = h.ndof * ws / (ms * 1e-3)
+
+    # ---- mixed-precision steps on the same data ----------------------------
+    tmx, smx = run(ldg.MODE_MIXED, args.steps, args.warmup)
+    ms_mx = float(np.mean(tmx))
+
+    # ---- end to end through the public API with host buffers ----------------
+    te2e, _ = run(ldg.MODE_FP64, max(2, args.steps // 2), 1, e2e=True)
+    ms_e2e = float(np.mean(te2e))
+
+    # ---- per-kernel timings on the launching stream -------------------------
+    Ut = torch.from_numpy(U0).cuda()
+    R = torch.empty_like(Ut)
+    t_res = kernel_ms(lambda: ldg.ldg_residual(h, Ut, R))
+    J64 = ldg.ldg_jacobian(h, Ut, ldg.PREC_FP64)
+    J32 = ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32)
+    t_j64 = kernel_ms(lambda: ldg.ldg_jacobian(h, Ut, ldg.PREC_FP64, J64))
+    t_j32 = kernel_ms(lambda: ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32, J32))
+    x64 = torch.randn(h.ndof, dtype=torch.float64, device="cuda")
+    y64 = torch.empty_like(x64)
+    x32, y32 = x64.float(), torch.empty(h.ndof, dtype=torch.float32, device="cuda")
+    t_mv64 = kernel_ms(lambda: ldg.ldg_jacvec(h, J64, 1.0, -0.033, x64, y64, ldg.PREC_FP64))
+    t_mv32 = kernel_ms(lambda: ldg.ldg_jacvec(h, J32, 1.0, -0.033, x32, y32, ldg.PREC_FP32))
+    P64 = ldg.ldg_precond(h, J64, 1.0, -0.033)
+    P32 = ldg.ldg_precond(h, J32, 1.0, -0.033)
+    t_pc64 = kernel_ms(lambda: ldg.ldg_precond(h, J64, 1.0, -0.033, P64), reps=5)
+    t_pc32 = kernel_ms(lambda: ldg.ldg_precond(h, J32, 1.0, -0.033, P32), reps=5)
+    t_ap64 = kernel_ms(lambda: ldg.ldg_precond_apply(h, P64, x64, y64, ldg.PREC_FP64))
+    t_ap32 = kernel_ms(lambda: ldg.ldg_precond_apply(h, P32, x32, y32, ldg.PREC_FP32))
+
+    # phase shares of the FP64 step (CUDA-event phase timers inside the step)
+    ph = {k: float(np.mean([s[k] for s in s64])) for k in
+          ("t_residual_ms", "t_jacobian_ms", "t_precond_ms", "t_linear_ms")}
+    hbm, src = _peaks()
+    res_fl = euler_residual_flops(h.D, h.p, h.nc, h.E)
+    kernels = {
+        "residual_fp64": {"ms": t_res, "dof_s": h.ndof / (t_res * 1e-3),
+                          "tflops": res_fl / (t_res * 1e-3) / 1e12},
+        "jacobian_fp64": {"ms": t_j64, "dof_s": h.ndof / (t_j64 * 1e-3)},
+        "jacobian_fp32": {"ms": t_j32, "dof_s": h.ndof / (t_j32 * 1e-3),
+                          "gbs": jac_bytes(h, 4) / (t_j32 * 1e-3) / 1e9},
+        "jacvec_fp64": {"ms": t_mv64, "gbs": jacvec_bytes(h, 8, 8) / (t_mv64 * 1e-3) / 1e9},
+        "jacvec_fp32": {"ms": t_mv32, "gbs": jacvec_bytes(h, 4, 4) / (t_mv32 * 1e-3) / 1e9},
+        "precond_build_fp64": {"ms": t_pc64}, "precond_build_fp32": {"ms": t_pc32},
+        "precond_apply_fp64": {"ms": t_ap64, "gbs": apply_bytes(h, 8, 8) / (t_ap64 * 1e-3) / 1e9},
+        "precond_apply_fp32": {"ms": t_ap32, "gbs": apply_bytes(h, 4, 4) / (t_ap32 * 1e-3) / 1e9},
+    }
+    # dominant kernel of the step by device-time share (ncu launch list,
+    # profiles/launches_euler2d_vortex_64x64_p4.md): the ILU(0) apply, bound by
+    # HBM (factors streamed once per apply); FP64 factors in the FP64 step
+    ab = apply_bytes(h, 8, 8)
+    roof = {"kernel": "k_precond_apply (FP64 factors, Euler 2-D p=4)", "bound": "hbm",
+            "achieved": ab / (t_ap64 * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": ab / (t_ap64 * 1e-3) / 1e9 / hbm, "traffic": None,
+            "bytes_per_launch": ab, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    kernels["residual_fp64"]["alu_frac_of_nominal_fp64"] = res_fl / (t_res * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+    out = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": h.E, "p": h.p, "dof": h.ndof,
+                   "newton_rtol": 1e-8, "linear": "GMRES(30) + element-block ILU(0), eta=1e-3",
+                   "jacobian": "rebuilt every step", "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{ws}"},
+        "newton_its": float(np.mean([s["newton_its"] for s in s64])),
+        "gmres_its": float(np.mean([s["gmres_its"] for s in s64])),
+        "phases_ms_fp64": ph,
+        "mixed": {"ms_per_step": ms_mx, "value": h.ndof * ws / (ms_mx * 1e-3),
+                  "speedup_vs_fp64": ms / ms_mx,
+                  "newton_its": float(np.mean([s["newton_its"] for s in smx])),
+                  "gmres_its": float(np.mean([s["gmres_its"] for s in smx])),
+                  "phases_ms": {k: float(np.mean([s[k] for s in smx])) for k in ph}},
+        "kernels": kernels,
+        "roofline": roof,
+        "hbm_peak_gbs": hbm, "hbm_peak_source": src,
+        "e2e": {"value": h.ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
+                "h2d_bytes_per_step": 2 * h.ndof * 8, "d2h_bytes_per_step": h.ndof * 8},
+        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_step(n_sample, p):
+    """One oracle BDF2 level (Newton-GMRES with the oracle's complex-step
+    Jacobian and ILU(0)) on an n_sample x n_sample patch of the workload."""
+    import numpy as np
+
+    from oracle import jacobian as JAC
+    from oracle import solvers as S
+    from oracle.residual import Discretization, full_residual
+    from paper_1204_1533_gb300 import inputs as I
+    L = 10.0 * n_sample / 64.0
+    m = I.vortex_mesh(n_sample, p, L=L)
+    disc = Discretization(m, EQ)
+    U0 = I.vortex_state(m, x0=L / 2, y0=L / 2)
+    pat = S.line_pattern(disc.D, disc.p)
+
+    def pc(K, shift, scale):
+        Fct = S.ilu0(S.masked_blocks(disc, K[0], shift, scale), pat)
+        return lambda v: S.ilu_apply(Fct, pat, v.reshape(U0.shape)).ravel()
+    F = lambda X: full_residual(disc, X)
+    jac = lambda X: (JAC.K11(disc, X), None, None)
+    t0 = time.perf_counter()
+    U1, st = S.newton_bdf2(F, jac, U0, U0, 0.05, first=False, rtol=1e-8, gmres_tol=1e-3,
+                           restart=30, reuse=15, precond_builder=pc)
+    return time.perf_counter() - t0, disc.ndof, st
+
+
+def cpu_baseline(args):
+    secs, dof, st = _oracle_step(args.cpu_sample, args.p)
+    return {"value": dof / secs, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"one BDF2 level (Newton-GMRES(30), ILU(0), complex-step Jacobian) on a "
+                      f"{args.cpu_sample}x{args.cpu_sample}-element patch of the p={args.p} vortex "
+                      f"({dof} DOF), {secs:.1f} s"}
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    times = []
+    dof = 0
+    for _ in range(args.warmup):
+        _oracle_step(args.cpu_sample, args.p)
+    for _ in range(args.steps):
+        s, dof, _ = _oracle_step(args.cpu_sample, args.p)
+        times.append(s)
+    mean = sum(times) / len(times)
+    v = dof / mean
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_elements": args.cpu_sample ** 2},
+        "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.cpu_sample}x{args.cpu_sample}-element patch, one BDF2 level per step"},
+        "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--cpu-sample", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -280,6 +280,10 @@ int ldg_newton_step(ldg_handle_t* h, double* U_next, const double* U_n, const do
                     const double* U_nm2, double dt, const ldg_solver_opts_t* opts,
                     ldg_step_stats_t* stats, void* stream);
 
+/* Number of kernels the library has launched since it was loaded (a host
+ * counter; for benchmarks that report launches per step). */
+int ldg_launch_count(long long* out);
+
 /* ||x||_2 of a device FP64 vector (synchronous; for drivers and tests). */
 int ldg_norm2(ldg_handle_t* h, const double* x, int64_t n, double* out, void* stream);
 

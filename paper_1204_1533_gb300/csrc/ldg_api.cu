@@ -3,7 +3,12 @@
 
 #include "ldg_internal.h"
 
+#include <atomic>
+
 namespace ldg {
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
 cudaError_t residual_2d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
 cudaError_t residual_3d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
 cudaError_t gradient_2d(const ldg_handle* h, const double* U, double* Q, cudaStream_t st);
@@ -87,10 +92,17 @@ extern "C" int ldg_norm2(ldg_handle_t* h, const double* x, int64_t n, double* ou
   const int blocks = 1024;
   k_sumsq<<<blocks, 256, 0, st>>>(x, n, h->red);
   k_sum_parts<<<1, 1024, 0, st>>>(h->red, blocks, h->red + blocks);
+  count_launch(2);
   double s = 0.0;
   LDG_CUDA_TRY(cudaMemcpyAsync(&s, h->red + blocks, sizeof(double), cudaMemcpyDeviceToHost, st));
   LDG_CUDA_TRY(cudaStreamSynchronize(st));
   if (!std::isfinite(s)) return LDG_ERR_NONFINITE;
   *out = std::sqrt(s);
+  return LDG_OK;
+}
+
+extern "C" int ldg_launch_count(long long* out) {
+  if (!out) return LDG_ERR_ARG;
+  *out = ldg::g_launches.load();
   return LDG_OK;
 }

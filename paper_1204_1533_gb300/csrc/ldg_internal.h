@@ -9,6 +9,9 @@
 
 namespace ldg {
 
+// number of kernels this library has launched (host-side counter)
+void count_launch(int n = 1);
+
 constexpr int MAXP = 7;
 constexpr int MAXP1 = MAXP + 1;
 constexpr int MAXQ = (3 * MAXP + 2) / 2;
@@ -72,6 +75,21 @@ struct ldg_handle {
   double* invJ = nullptr;
   double* gD = nullptr;
   double* src = nullptr;
+  int8_t* nbf = nullptr;     // neighbour face id per element face [E][2D] (-1: boundary)
+  std::vector<int8_t> nbf_h;
+  int16_t* pat = nullptr;    // element Line-DG pattern: sorted columns of each row [npe][Dp+1]
+  int8_t* slot = nullptr;    // column slot of node j in row i, or -1 [npe][npe]
+  int16_t* lvl = nullptr;    // rows sorted by wavefront level (sum of indices) [npe]
+  int32_t* lvl_ptr = nullptr; // level start offsets [D p + 2]
+  bool has_wall = false;
+  // Newton-Krylov state kept across time steps (Jacobian re-use, Sec. 4.3)
+  struct ldg_jac* Jn = nullptr;
+  struct ldg_pc* Pn = nullptr;
+  int jac_age = 0;
+  int jac_mode = -1;
+  double pc_adt = 0.0;
+  void* ws = nullptr;        // solver workspace
+  size_t ws_bytes = 0;
   double* Qbuf = nullptr;    // LDG gradient of the last residual [E][nc][D][npe]
   double* red = nullptr;     // reduction scratch (doubles)
   int64_t red_len = 0;
@@ -88,7 +106,48 @@ struct ldg_handle {
     return g;
   }
   bool viscous() const { return kind == LDG_EQ_NAVIER_STOKES || kind == LDG_EQ_POISSON; }
+  int64_t nlines() const { return E * D * nl; }
+  int64_t ntiles() const { return (nlines() + 31) / 32; }
+  int pat_w() const { return D * p + 1; }
+  int nk11() const { return ((p + 1) * (p + 1) + 2 * (p + 1)) * nc * nc; }
+  int nk12() const { return viscous() ? ((p + 1) * (p + 1) + (p + 1)) * nc * nc * D : 0; }
+  int nk21() const { return viscous() ? ((p + 1) * (p + 1) + (p + 1)) * D : 0; }
 };
+
+// Line-sparse Jacobian: K11, K12, K21 in 32-line tiles, entry-major inside a
+// tile: value k of line L sits at ((L / 32) nk + k) 32 + L % 32.
+struct ldg_jac {
+  ldg_handle* h = nullptr;
+  int prec = 0;
+  bool built = false;
+  bool k21_built = false;
+  void* K11 = nullptr;
+  void* K12 = nullptr;
+  void* K21 = nullptr;
+  void* gbuf = nullptr;   // K21 x workspace [E][nc][D][npe] in the vector precision (double)
+};
+
+// Element-block ILU(0) factors [E][npe][Dp+1][nc][nc] and inverted diagonal
+// blocks of U [E][npe][nc][nc], at the Jacobian's precision.
+struct ldg_pc {
+  ldg_handle* h = nullptr;
+  int prec = 0;
+  bool built = false;
+  void* F = nullptr;
+  void* Dinv = nullptr;
+};
+
+namespace ldg {
+cudaError_t launch_jacobian(const ldg_handle* h, const double* U, const double* Q, ldg_jac* J,
+                            cudaStream_t st);
+cudaError_t launch_k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st);
+cudaError_t launch_jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                          const void* x, void* y, int vprec, cudaStream_t st);
+cudaError_t launch_precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                           ldg_pc* P, cudaStream_t st);
+cudaError_t launch_precond_apply(const ldg_handle* h, const ldg_pc* P, const void* r, void* z,
+                                 int vprec, cudaStream_t st);
+}  // namespace ldg
 
 #define LDG_CUDA_TRY(x)                      \
   do {                                       \

@@ -1,0 +1,191 @@
+// C-ABI entry points of the Jacobian, split matvec and preconditioner.
+#include <cstring>
+#include <vector>
+
+#include "ldg_ops.h"
+
+namespace ldg {
+
+#define LDG_DISPATCH(h, CALL)                              \
+  do {                                                     \
+    if ((h)->D == 2) {                                     \
+      switch ((h)->kind) {                                 \
+        case LDG_EQ_POISSON: return Ops<2, 0>::CALL;       \
+        case LDG_EQ_EULER: return Ops<2, 1>::CALL;         \
+        case LDG_EQ_NAVIER_STOKES: return Ops<2, 2>::CALL; \
+        case LDG_EQ_ADVECTION: return Ops<2, 3>::CALL;     \
+      }                                                    \
+    } else if ((h)->D == 3) {                              \
+      switch ((h)->kind) {                                 \
+        case LDG_EQ_EULER: return Ops<3, 1>::CALL;         \
+        case LDG_EQ_NAVIER_STOKES: return Ops<3, 2>::CALL; \
+      }                                                    \
+    }                                                      \
+  } while (0)
+
+bool ops_supported(const ldg_handle* h) {
+  if (h->p < 1 || h->p > 4 || h->has_wall) return false;
+  if (h->D == 2) return true;
+  return h->kind == LDG_EQ_EULER || h->kind == LDG_EQ_NAVIER_STOKES;
+}
+
+cudaError_t launch_jacobian(const ldg_handle* h, const double* U, const double* Q, ldg_jac* J,
+                            cudaStream_t st) {
+  LDG_DISPATCH(h, jacobian(h, U, Q, J, st));
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st) {
+  LDG_DISPATCH(h, k21(h, J, st));
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                          const void* x, void* y, int vprec, cudaStream_t st) {
+  LDG_DISPATCH(h, jacvec(h, J, shift, scale, x, y, vprec, st));
+  return cudaErrorInvalidValue;
+}
+static size_t precond_smem(const ldg_handle* h, int prec) {
+  LDG_DISPATCH(h, precond_smem(h->p, prec));
+  return 0;
+}
+cudaError_t launch_precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                           ldg_pc* P, cudaStream_t st) {
+  LDG_DISPATCH(h, precond(h, J, shift, scale, P, st));
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_precond_apply(const ldg_handle* h, const ldg_pc* P, const void* r, void* z,
+                                 int vprec, cudaStream_t st) {
+  LDG_DISPATCH(h, apply(h, P, r, z, vprec, st));
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ldg
+
+using namespace ldg;
+
+static size_t esize(int prec) { return prec == LDG_PREC_FP32 ? 4 : 8; }
+
+extern "C" int ldg_jac_destroy(ldg_jac_t* J) {
+  if (!J) return LDG_OK;
+  cudaFree(J->K11);
+  cudaFree(J->K12);
+  cudaFree(J->K21);
+  cudaFree(J->gbuf);
+  delete J;
+  return LDG_OK;
+}
+
+extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_t** Jp, void* stream) {
+  if (!h || !U || !Jp || (prec != LDG_PREC_FP32 && prec != LDG_PREC_FP64)) return LDG_ERR_ARG;
+  if (!ops_supported(h)) return LDG_ERR_UNSUPPORTED;
+  ldg_jac* J = *Jp;
+  if (J && (J->h != h || J->prec != prec)) return LDG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!J) {
+    J = new ldg_jac();
+    J->h = h;
+    J->prec = prec;
+    const size_t rows = (size_t)h->ntiles() * 32;
+    cudaError_t err = cudaMalloc(&J->K11, rows * h->nk11() * esize(prec));
+    if (err == cudaSuccess) err = cudaMemset(J->K11, 0, rows * h->nk11() * esize(prec));
+    if (err == cudaSuccess && h->viscous()) {
+      err = cudaMalloc(&J->K12, rows * h->nk12() * esize(prec));
+      if (err == cudaSuccess) err = cudaMemset(J->K12, 0, rows * h->nk12() * esize(prec));
+      if (err == cudaSuccess) err = cudaMalloc(&J->K21, rows * h->nk21() * esize(prec));
+      if (err == cudaSuccess) err = cudaMemset(J->K21, 0, rows * h->nk21() * esize(prec));
+      if (err == cudaSuccess) err = cudaMalloc(&J->gbuf, (size_t)h->ndof * h->D * sizeof(double));
+    }
+    if (err != cudaSuccess) {
+      ldg_jac_destroy(J);
+      return LDG_ERR_CUDA;
+    }
+  }
+  if (h->viscous() && launch_gradient(h, U, h->Qbuf, st) != cudaSuccess) return LDG_ERR_CUDA;
+  if (launch_jacobian(h, U, h->Qbuf, J, st) != cudaSuccess) return LDG_ERR_CUDA;
+  if (h->viscous() && !J->k21_built) {
+    if (launch_k21(h, J, st) != cudaSuccess) return LDG_ERR_CUDA;
+    J->k21_built = true;
+  }
+  J->built = true;
+  *Jp = J;
+  return LDG_OK;
+}
+
+extern "C" int ldg_jac_export(const ldg_jac_t* J, void* K11, void* K12, void* K21) {
+  if (!J || !J->built) return LDG_ERR_NOT_BUILT;
+  const ldg_handle* h = J->h;
+  const size_t es = esize(J->prec);
+  const int64_t NL = h->nlines(), rows = h->ntiles() * 32;
+  auto untile = [&](const void* dev, void* host, int nk) -> int {
+    std::vector<unsigned char> tmp((size_t)rows * nk * es);
+    if (cudaMemcpy(tmp.data(), dev, tmp.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return LDG_ERR_CUDA;
+    unsigned char* out = (unsigned char*)host;
+    for (int64_t L = 0; L < NL; ++L)
+      for (int k = 0; k < nk; ++k)
+        std::memcpy(out + ((size_t)k * NL + L) * es, tmp.data() + (((L >> 5) * nk + k) * 32 + (L & 31)) * es, es);
+    return LDG_OK;
+  };
+  int rc = LDG_OK;
+  if (K11) rc = untile(J->K11, K11, h->nk11());
+  if (rc == LDG_OK && K12 && h->viscous()) rc = untile(J->K12, K12, h->nk12());
+  if (rc == LDG_OK && K21 && h->viscous()) rc = untile(J->K21, K21, h->nk21());
+  return rc;
+}
+
+extern "C" int ldg_jacvec(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, const void* x,
+                          void* y, int prec, void* stream) {
+  if (!h || !J || !x || !y || J->h != h) return LDG_ERR_ARG;
+  if (!J->built) return LDG_ERR_NOT_BUILT;
+  if (prec != LDG_PREC_FP32 && prec != LDG_PREC_FP64) return LDG_ERR_ARG;
+  if (J->prec == LDG_PREC_FP64 && prec == LDG_PREC_FP32) return LDG_ERR_UNSUPPORTED;
+  return launch_jacvec(h, J, shift, scale, x, y, prec, (cudaStream_t)stream) == cudaSuccess ? LDG_OK
+                                                                                          : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_pc_destroy(ldg_pc_t* P) {
+  if (!P) return LDG_OK;
+  cudaFree(P->F);
+  cudaFree(P->Dinv);
+  delete P;
+  return LDG_OK;
+}
+
+extern "C" int ldg_precond(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, ldg_pc_t** Pp,
+                           void* stream) {
+  if (!h || !J || !Pp || J->h != h) return LDG_ERR_ARG;
+  if (!J->built) return LDG_ERR_NOT_BUILT;
+  if (precond_smem(h, J->prec) > 227 * 1024) return LDG_ERR_UNSUPPORTED;
+  ldg_pc* P = *Pp;
+  if (P && (P->h != h || P->prec != J->prec)) return LDG_ERR_ARG;
+  if (!P) {
+    P = new ldg_pc();
+    P->h = h;
+    P->prec = J->prec;
+    const size_t bb = (size_t)h->nc * h->nc;
+    cudaError_t err = cudaMalloc(&P->F, (size_t)h->E * h->npe * h->pat_w() * bb * esize(J->prec));
+    if (err == cudaSuccess) err = cudaMalloc(&P->Dinv, (size_t)h->E * h->npe * bb * esize(J->prec));
+    if (err != cudaSuccess) {
+      ldg_pc_destroy(P);
+      return LDG_ERR_CUDA;
+    }
+  }
+  if (launch_precond(h, J, shift, scale, P, (cudaStream_t)stream) != cudaSuccess) return LDG_ERR_CUDA;
+  P->built = true;
+  *Pp = P;
+  return LDG_OK;
+}
+
+extern "C" int ldg_precond_apply(ldg_handle_t* h, const ldg_pc_t* P, const void* r, void* z, int prec,
+                                 void* stream) {
+  if (!h || !P || !r || !z || P->h != h) return LDG_ERR_ARG;
+  if (!P->built) return LDG_ERR_NOT_BUILT;
+  if (prec != P->prec) return LDG_ERR_UNSUPPORTED;
+  return launch_precond_apply(h, P, r, z, prec, (cudaStream_t)stream) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_pc_export(const ldg_pc_t* P, void* factors) {
+  if (!P || !factors) return LDG_ERR_ARG;
+  if (!P->built) return LDG_ERR_NOT_BUILT;
+  const ldg_handle* h = P->h;
+  const size_t bytes = (size_t)h->E * h->npe * h->pat_w() * h->nc * h->nc * esize(P->prec);
+  return cudaMemcpy(factors, P->F, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
+}

@@ -1,0 +1,141 @@
+// Definitions of Ops<D, EQ>: runtime degree -> templated launchers.
+#pragma once
+#include "ldg_linalg_impl.cuh"
+#include "ldg_ops.h"
+
+namespace ldg {
+
+#define LDG_FOR_P(F) \
+  switch (h->p) {    \
+    case 1:          \
+      F(1);          \
+    case 2:          \
+      F(2);          \
+    case 3:          \
+      F(3);          \
+    case 4:          \
+      F(4);          \
+    default:         \
+      break;         \
+  }
+
+template <int D, int EQ>
+bool Ops<D, EQ>::supported(int p) {
+  return p >= 1 && p <= 4;
+}
+
+template <int D, int EQ>
+cudaError_t Ops<D, EQ>::jacobian(const ldg_handle* h, const double* U, const double* Q, ldg_jac* J,
+                                 cudaStream_t st) {
+  if (J->prec == LDG_PREC_FP32) {
+#define F(P) return run_jacobian<D, P, EQ, float>(h, U, Q, (float*)J->K11, (float*)J->K12, st)
+    LDG_FOR_P(F)
+#undef F
+  } else {
+#define F(P) return run_jacobian<D, P, EQ, double>(h, U, Q, (double*)J->K11, (double*)J->K12, st)
+    LDG_FOR_P(F)
+#undef F
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int EQ>
+cudaError_t Ops<D, EQ>::k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st) {
+  if (J->prec == LDG_PREC_FP32) {
+#define F(P) return run_k21<D, P, float>(h, (float*)J->K21, st)
+    LDG_FOR_P(F)
+#undef F
+  } else {
+#define F(P) return run_k21<D, P, double>(h, (double*)J->K21, st)
+    LDG_FOR_P(F)
+#undef F
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int EQ>
+cudaError_t Ops<D, EQ>::jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                               const void* x, void* y, int vprec, cudaStream_t st) {
+  if (J->prec == LDG_PREC_FP32 && vprec == LDG_PREC_FP32) {
+#define F(P)                                                                                      \
+  return run_jacvec<D, P, EQ, float, float>(h, (const float*)J->K11, (const float*)J->K12,         \
+                                            (const float*)J->K21, (float*)J->gbuf, shift, scale, \
+                                            (const float*)x, (float*)y, st)
+    LDG_FOR_P(F)
+#undef F
+  } else if (J->prec == LDG_PREC_FP32) {
+#define F(P)                                                                                        \
+  return run_jacvec<D, P, EQ, float, double>(h, (const float*)J->K11, (const float*)J->K12,          \
+                                             (const float*)J->K21, (double*)J->gbuf, shift, scale, \
+                                             (const double*)x, (double*)y, st)
+    LDG_FOR_P(F)
+#undef F
+  } else if (vprec == LDG_PREC_FP64) {
+#define F(P)                                                                                          \
+  return run_jacvec<D, P, EQ, double, double>(h, (const double*)J->K11, (const double*)J->K12,         \
+                                              (const double*)J->K21, (double*)J->gbuf, shift, scale, \
+                                              (const double*)x, (double*)y, st)
+    LDG_FOR_P(F)
+#undef F
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int EQ>
+size_t Ops<D, EQ>::precond_smem(int p, int prec) {
+  const bool f = prec == LDG_PREC_FP32;
+  switch (p) {
+    case 1:
+      return f ? ldg::precond_smem<D, 1, EQ, float>() : ldg::precond_smem<D, 1, EQ, double>();
+    case 2:
+      return f ? ldg::precond_smem<D, 2, EQ, float>() : ldg::precond_smem<D, 2, EQ, double>();
+    case 3:
+      return f ? ldg::precond_smem<D, 3, EQ, float>() : ldg::precond_smem<D, 3, EQ, double>();
+    case 4:
+      return f ? ldg::precond_smem<D, 4, EQ, float>() : ldg::precond_smem<D, 4, EQ, double>();
+  }
+  return 0;
+}
+
+template <int D, int EQ>
+cudaError_t Ops<D, EQ>::precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                                ldg_pc* P, cudaStream_t st) {
+  if (J->prec == LDG_PREC_FP32) {
+#define F(PP)                                                                                   \
+  return run_precond<D, PP, EQ, float>(h, (const float*)J->K11, (const float*)J->K12,           \
+                                       (const float*)J->K21, (float*)P->F, (float*)P->Dinv, shift, \
+                                       scale, st)
+    LDG_FOR_P(F)
+#undef F
+  } else {
+#define F(PP)                                                                                       \
+  return run_precond<D, PP, EQ, double>(h, (const double*)J->K11, (const double*)J->K12,            \
+                                        (const double*)J->K21, (double*)P->F, (double*)P->Dinv, shift, \
+                                        scale, st)
+    LDG_FOR_P(F)
+#undef F
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int EQ>
+cudaError_t Ops<D, EQ>::apply(const ldg_handle* h, const ldg_pc* P, const void* r, void* z, int vprec,
+                              cudaStream_t st) {
+  if (P->prec == LDG_PREC_FP32 && vprec == LDG_PREC_FP32) {
+#define F(PP)                                                                                     \
+  return run_precond_apply<D, PP, EQ, float, float>(h, (const float*)P->F, (const float*)P->Dinv, \
+                                                    (const float*)r, (float*)z, st)
+    LDG_FOR_P(F)
+#undef F
+  } else if (P->prec == LDG_PREC_FP64 && vprec == LDG_PREC_FP64) {
+#define F(PP)                                                                                        \
+  return run_precond_apply<D, PP, EQ, double, double>(h, (const double*)P->F, (const double*)P->Dinv, \
+                                                      (const double*)r, (double*)z, st)
+    LDG_FOR_P(F)
+#undef F
+  }
+  return cudaErrorInvalidValue;
+}
+
+#undef LDG_FOR_P
+}  // namespace ldg

@@ -330,6 +330,7 @@ cudaError_t run_gradient(const ldg_handle* h, const double* U, double* Q, cudaSt
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
   kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, h->geo(), h->tab, h->phys);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -346,6 +347,7 @@ cudaError_t run_residual(const ldg_handle* h, const double* U, const double* Q, 
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
   kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, R, h->geo(), h->tab, h->phys);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -247,6 +247,9 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
   h->phys.nbc = eq->n_bc;
   for (int t = 0; t < ldg::MAXBC; ++t)
     h->phys.bck[t] = (t < eq->n_bc && eq->bc_kind) ? eq->bc_kind[t] : LDG_BC_DIRICHLET;
+  for (int64_t k = 0; k < E * 2 * D; ++k)
+    if (mesh->btag[k] >= 0 && mesh->btag[k] < ldg::MAXBC && h->phys.bck[mesh->btag[k]] == LDG_BC_WALL)
+      h->has_wall = true;
   std::vector<ld> Dnode;
   int rc = build_tables(s, p, h->tab, Dnode, h->nq);
   if (rc != LDG_OK) {
@@ -362,6 +365,8 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
           h->nbr_h[((e * D + d) * nl + l) * 2 + end] = (int32_t)g;
         }
       }
+  h->nbf_h.assign(E * 2 * D, -1);
+  for (int64_t k = 0; k < E * 2 * D; ++k) h->nbf_h[k] = (int8_t)nb_f[k];
   // ---- switch function -------------------------------------------------------
   h->sw_h.assign(E * D * 2, 0);
   for (int64_t e0 = 0; e0 < E; ++e0)
@@ -513,8 +518,42 @@ extern "C" int ldg_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_
     err = up((void**)&h->gD, eq->g_D, (size_t)h->ndof * sizeof(double));
   if (err == cudaSuccess && eq->source)
     err = up((void**)&h->src, eq->source, (size_t)h->ndof * sizeof(double));
+  if (err == cudaSuccess) err = up((void**)&h->nbf, h->nbf_h.data(), h->nbf_h.size());
   if (err == cudaSuccess && h->viscous())
     err = cudaMalloc((void**)&h->Qbuf, (size_t)h->ndof * D * sizeof(double));
+  if (err == cudaSuccess) {
+    // element Line-DG pattern (Sec. 2.3): row i couples to the D p + 1 nodes
+    // of its lines; wavefront levels i + j + k order the triangular solves
+    const int n = h->p + 1, npe = h->npe, W = h->pat_w();
+    std::vector<int16_t> pat((size_t)npe * W), lvl(npe);
+    std::vector<int8_t> slot((size_t)npe * npe, -1);
+    std::vector<int32_t> lptr(D * h->p + 2, 0);
+    for (int i = 0; i < npe; ++i) {
+      const int ii[3] = {i % n, (i / n) % n, (i / (n * n)) % n};
+      std::vector<int> cols;
+      for (int j = 0; j < npe; ++j) {
+        const int jj[3] = {j % n, (j / n) % n, (j / (n * n)) % n};
+        int diff = 0;
+        for (int b = 0; b < D; ++b) diff += (ii[b] != jj[b]);
+        if (diff <= 1) cols.push_back(j);
+      }
+      for (int s = 0; s < W; ++s) {
+        pat[(size_t)i * W + s] = (int16_t)cols[s];
+        slot[(size_t)i * npe + cols[s]] = (int8_t)s;
+      }
+      lptr[ii[0] + ii[1] + ii[2] + 1]++;
+    }
+    for (int k = 1; k < (int)lptr.size(); ++k) lptr[k] += lptr[k - 1];
+    std::vector<int32_t> fill(lptr.begin(), lptr.end());
+    for (int i = 0; i < npe; ++i) {
+      const int lv = (i % n) + ((i / n) % n) + ((i / (n * n)) % n);
+      lvl[fill[lv]++] = (int16_t)i;
+    }
+    err = up((void**)&h->pat, pat.data(), pat.size() * sizeof(int16_t));
+    if (err == cudaSuccess) err = up((void**)&h->slot, slot.data(), slot.size());
+    if (err == cudaSuccess) err = up((void**)&h->lvl, lvl.data(), lvl.size() * sizeof(int16_t));
+    if (err == cudaSuccess) err = up((void**)&h->lvl_ptr, lptr.data(), lptr.size() * sizeof(int32_t));
+  }
   if (err == cudaSuccess) {
     h->red_len = 4096;
     err = cudaMalloc((void**)&h->red, h->red_len * sizeof(double));
@@ -557,6 +596,9 @@ extern "C" int ldg_setup_host(const ldg_mesh_t* mesh, const ldg_equations_t* eq,
 
 extern "C" int ldg_destroy(ldg_handle_t* h) {
   if (!h) return LDG_OK;
+  ldg_jac_destroy(h->Jn);
+  ldg_pc_destroy(h->Pn);
+  cudaFree(h->ws);
   cudaFree(h->nbr);
   cudaFree(h->sw);
   cudaFree(h->ng);
@@ -566,17 +608,20 @@ extern "C" int ldg_destroy(ldg_handle_t* h) {
   cudaFree(h->src);
   cudaFree(h->Qbuf);
   cudaFree(h->red);
+  cudaFree(h->nbf);
+  cudaFree(h->pat);
+  cudaFree(h->slot);
+  cudaFree(h->lvl);
+  cudaFree(h->lvl_ptr);
   delete h;
   return LDG_OK;
 }
 
 extern "C" int ldg_info(const ldg_handle_t* h, int64_t info[10]) {
   if (!h || !info) return LDG_ERR_ARG;
-  const int64_t NL = h->E * h->D * h->nl;
-  const int n = h->p + 1;
-  const int64_t k11 = (int64_t)(n * n + 2 * n) * h->nc * h->nc;
-  const int64_t k12 = h->viscous() ? (int64_t)(n * n + n) * h->nc * h->nc * h->D : 0;
-  int64_t v[10] = {h->D, h->p, h->nc, h->E, h->npe, h->nl, h->nq, h->ndof, k11 * NL, k12 * NL};
+  const int64_t NL = h->nlines();
+  int64_t v[10] = {h->D,  h->p,  h->nc,   h->E, h->npe, h->nl, h->nq, h->ndof, (int64_t)h->nk11() * NL,
+                   (int64_t)h->nk12() * NL};
   for (int i = 0; i < 10; ++i) info[i] = v[i];
   return LDG_OK;
 }

@@ -1,0 +1,435 @@
+// BDF2 Newton-GMRES step (Sec. 4.2-4.3, Eqs. 39-41) with Jacobian re-use.
+//
+// G(U) = U - c1 U^n - c2 U^{n-1} - alpha dt R(U)  (BDF2: c1 = 4/3,
+// c2 = -1/3, alpha = 2/3; BDF1: 1, 0, 1). Each Newton iteration solves
+// (I - alpha dt A) delta = -G(U) with right-preconditioned GMRES(m): the
+// Krylov basis is orthogonalised by classical Gram-Schmidt with one
+// re-orthogonalisation pass (two batched-dot + update sweeps per
+// iteration), the small Hessenberg least-squares problem is kept on the
+// host. In the mixed mode the basis, matrix values and ILU factors are FP32
+// and each linear solve is wrapped in FP64 iterative refinement: the
+// residual -G - (I - alpha dt A) delta is formed with FP64 vectors, solved
+// to a relative tolerance in FP32, and the correction added in FP64. The
+// nonlinear residual, the update and the convergence test are FP64.
+// The Jacobian and preconditioner are rebuilt when the Newton iterations
+// since the last rebuild exceed `reuse` (the paper's policy) or when a
+// Newton step fails to halve ||G||.
+#include <cmath>
+#include <vector>
+
+#include "ldg_internal.h"
+
+namespace ldg {
+
+constexpr int MDOT_BLOCKS = 296;
+
+template <typename V>
+__global__ void k_mdot(const V* __restrict__ Vb, int64_t n, const V* __restrict__ w,
+                       double* __restrict__ part) {
+  const V* v = Vb + (int64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)v[i] * (double)w[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_rows(const double* __restrict__ part, int nblk, double* __restrict__ out,
+                              double* __restrict__ accum) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[blockIdx.x * nblk + i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+      out[blockIdx.x] = s;
+      if (accum) accum[blockIdx.x] += s;
+    }
+  }
+}
+
+// w -= sum_j h_j V_j  (h on the device)
+template <typename V>
+__global__ void k_maxpy(V* __restrict__ w, const V* __restrict__ Vb, const double* __restrict__ h, int k,
+                        int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = (double)w[i];
+    for (int j = 0; j < k; ++j) s -= h[j] * (double)Vb[(int64_t)j * n + i];
+    w[i] = (V)s;
+  }
+}
+
+// dst = sum_j y_j V_j  (y on the device)
+template <typename V>
+__global__ void k_combine(V* __restrict__ dst, const V* __restrict__ Vb, const double* __restrict__ y, int k,
+                          int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += y[j] * (double)Vb[(int64_t)j * n + i];
+    dst[i] = (V)s;
+  }
+}
+
+template <typename A, typename B>
+__global__ void k_scale_to(B* __restrict__ dst, const A* __restrict__ src, double s, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (B)(s * (double)src[i]);
+}
+
+// y += a * x (x of any precision)
+template <typename X>
+__global__ void k_axpy_d(double* __restrict__ y, const X* __restrict__ x, double a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * (double)x[i];
+}
+
+// G = U - c1 Un - c2 Unm1 - adt R
+__global__ void k_bdf_residual(double* __restrict__ G, const double* __restrict__ U, const double* __restrict__ Un,
+                               const double* __restrict__ Unm1, const double* __restrict__ R, double c1, double c2,
+                               double adt, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double g = U[i] - c1 * Un[i] - adt * R[i];
+    if (Unm1) g -= c2 * Unm1[i];
+    G[i] = g;
+  }
+}
+
+__global__ void k_extrap(double* __restrict__ U, const double* __restrict__ Un, const double* __restrict__ Unm1,
+                         int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    U[i] = Unm1 ? 2.0 * Un[i] - Unm1[i] : Un[i];
+}
+
+inline unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+// ---------------------------------------------------------------------------
+struct Work {
+  double *R, *G, *U0, *delta, *r64, *tmp64;  // FP64 vectors
+  void* Vb;                                   // Krylov basis [(m+1) N] (float or double)
+  void *z, *t;                                // precision of the basis
+  double* part;                               // [ (m+2) * MDOT_BLOCKS ]
+  double* hcol;                               // [m+2]
+  double* hacc;                               // [m+2]
+  double* y;                                  // [m+1]
+};
+
+static size_t work_bytes(const ldg_handle* h, int m, int vbytes) {
+  const size_t N = (size_t)h->ndof;
+  return 6 * N * 8 + (size_t)(m + 1) * N * vbytes + 2 * N * vbytes + (size_t)(m + 2) * MDOT_BLOCKS * 8 +
+         3 * (size_t)(m + 2) * 8 + 64 * 256;  // plus 256-byte alignment of each piece
+}
+
+static int get_work(ldg_handle* h, int m, int vbytes, Work& w) {
+  const size_t need = work_bytes(h, m, 8);  // sized for FP64 so either mode fits
+  if (h->ws_bytes < need) {
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    if (cudaMalloc(&h->ws, need) != cudaSuccess) return LDG_ERR_CUDA;
+    h->ws_bytes = need;
+  }
+  const size_t N = (size_t)h->ndof;
+  char* p = (char*)h->ws;
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) / 256 * 256;
+    return r;
+  };
+  w.R = (double*)take(N * 8);
+  w.G = (double*)take(N * 8);
+  w.U0 = (double*)take(N * 8);
+  w.delta = (double*)take(N * 8);
+  w.r64 = (double*)take(N * 8);
+  w.tmp64 = (double*)take(N * 8);
+  w.Vb = take((size_t)(m + 1) * N * vbytes);
+  w.z = take(N * vbytes);
+  w.t = take(N * vbytes);
+  w.part = (double*)take((size_t)(m + 2) * MDOT_BLOCKS * 8);
+  w.hcol = (double*)take((size_t)(m + 2) * 8);
+  w.hacc = (double*)take((size_t)(m + 2) * 8);
+  w.y = (double*)take((size_t)(m + 2) * 8);
+  return (size_t)(p - (char*)h->ws) <= h->ws_bytes ? LDG_OK : LDG_ERR_CUDA;
+}
+
+// dot products of k basis vectors with w: into dev[0..k-1] (and accum)
+template <typename V>
+static cudaError_t mdot(const V* Vb, int k, int64_t n, const V* w, double* part, double* dev, double* accum,
+                        cudaStream_t st) {
+  dim3 grid(MDOT_BLOCKS, k);
+  k_mdot<V><<<grid, 256, 0, st>>>(Vb, n, w, part);
+  count_launch();
+  k_reduce_rows<<<k, 256, 0, st>>>(part, MDOT_BLOCKS, dev, accum);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Right-preconditioned GMRES(m) on (I - adt A) x = b for vectors of type V;
+// b is overwritten; x receives the solution (zero initial guess).
+template <typename V>
+static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double tol, int m, Work& w,
+                 int* its_out, double* rel_out, cudaStream_t st) {
+  const int64_t n = h->ndof;
+  V* Vb = (V*)w.Vb;
+  V* z = (V*)w.z;
+  V* t = (V*)w.t;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(m + 2);
+  // beta = ||b||
+  if (mdot<V>(b, 1, n, b, w.part, w.hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
+  double bb = 0;
+  LDG_CUDA_TRY(cudaMemcpyAsync(&bb, w.hcol, 8, cudaMemcpyDeviceToHost, st));
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(bb)) return LDG_ERR_NONFINITE;
+  const double beta = std::sqrt(bb);
+  *its_out = 0;
+  *rel_out = 0.0;
+  if (beta == 0.0) {
+    LDG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(V), st));
+    return LDG_OK;
+  }
+  k_scale_to<V, V><<<grid_for(n), 256, 0, st>>>(Vb, b, 1.0 / beta, n);
+  count_launch();
+  g[0] = beta;
+  int k_used = 0;
+  double rel = 1.0;
+  for (int k = 0; k < m; ++k) {
+    V* vk = Vb + (int64_t)k * n;
+    V* vn = Vb + (int64_t)(k + 1) * n;
+    if (launch_precond_apply(h, h->Pn, vk, z, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
+    if (launch_jacvec(h, h->Jn, 1.0, -adt, z, vn, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
+    // classical Gram-Schmidt, twice
+    LDG_CUDA_TRY(cudaMemsetAsync(w.hacc, 0, (k + 2) * sizeof(double), st));
+    for (int pass = 0; pass < 2; ++pass) {
+      if (mdot<V>(Vb, k + 1, n, vn, w.part, w.hcol, w.hacc, st) != cudaSuccess) return LDG_ERR_CUDA;
+      k_maxpy<V><<<grid_for(n), 256, 0, st>>>(vn, Vb, w.hcol, k + 1, n);
+      count_launch();
+    }
+    if (mdot<V>(vn, 1, n, vn, w.part, w.hacc + k + 1, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
+    LDG_CUDA_TRY(cudaMemcpyAsync(hc.data(), w.hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LDG_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
+    const double hn = std::sqrt(hc[k + 1]);
+    if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
+    H[(size_t)(k + 1) * m + k] = hn;
+    if (hn > 0) k_scale_to<V, V><<<grid_for(n), 256, 0, st>>>(vn, vn, 1.0 / hn, n);
+    count_launch();
+    for (int j = 0; j < k; ++j) {
+      const double a = H[(size_t)j * m + k], c = H[(size_t)(j + 1) * m + k];
+      H[(size_t)j * m + k] = cs[j] * a + sn[j] * c;
+      H[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * c;
+    }
+    const double a = H[(size_t)k * m + k], c = H[(size_t)(k + 1) * m + k];
+    const double den = std::hypot(a, c);
+    if (den == 0.0) return LDG_ERR_GMRES_BREAKDOWN;
+    cs[k] = a / den;
+    sn[k] = c / den;
+    H[(size_t)k * m + k] = den;
+    H[(size_t)(k + 1) * m + k] = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    k_used = k + 1;
+    rel = std::fabs(g[k + 1]) / beta;
+    if (rel <= tol || hn == 0.0) break;
+  }
+  std::vector<double> yv(k_used);
+  for (int i = k_used - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int j = i + 1; j < k_used; ++j) s -= H[(size_t)i * m + j] * yv[j];
+    yv[i] = s / H[(size_t)i * m + i];
+  }
+  LDG_CUDA_TRY(cudaMemcpyAsync(w.y, yv.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, st));
+  k_combine<V><<<grid_for(n), 256, 0, st>>>(t, Vb, w.y, k_used, n);
+  count_launch();
+  if (launch_precond_apply(h, h->Pn, t, x, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  *its_out = k_used;
+  *rel_out = rel;
+  return LDG_OK;
+}
+
+static int norm2(ldg_handle* h, const double* x, double* out, Work& w, cudaStream_t st) {
+  if (mdot<double>(x, 1, h->ndof, x, w.part, w.hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
+  double s = 0;
+  LDG_CUDA_TRY(cudaMemcpyAsync(&s, w.hcol, 8, cudaMemcpyDeviceToHost, st));
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(s)) return LDG_ERR_NONFINITE;
+  *out = std::sqrt(s);
+  return LDG_OK;
+}
+
+bool ops_supported(const ldg_handle* h);
+
+}  // namespace ldg
+
+using namespace ldg;
+
+struct PhaseTimer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  double* acc;
+  PhaseTimer(cudaStream_t s, double* out) : st(s), acc(out) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  ~PhaseTimer() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    *acc += ms;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, const double* Unm1,
+                               const double* Unm2, double dt, const ldg_solver_opts_t* o,
+                               ldg_step_stats_t* stats, void* stream) {
+  (void)Unm2;
+  if (!h || !U || !Un || !o || !stats || !(dt > 0)) return LDG_ERR_ARG;
+  if (!o->first_step && !Unm1) return LDG_ERR_ARG;
+  if (o->restart < 1 || o->restart > 64 || o->max_newton < 1) return LDG_ERR_ARG;
+  if (!ops_supported(h)) return LDG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int mode = o->mode == LDG_MODE_FP64 ? LDG_MODE_FP64 : LDG_MODE_MIXED;
+  const int vprec = mode == LDG_MODE_FP64 ? LDG_PREC_FP64 : LDG_PREC_FP32;
+  *stats = ldg_step_stats_t{};
+  Work w;
+  int rc = get_work(h, o->restart, vprec == LDG_PREC_FP32 ? 4 : 8, w);
+  if (rc) return rc;
+  const int64_t n = h->ndof;
+  const bool first = o->first_step != 0;
+  const double alpha = first ? 1.0 : 2.0 / 3.0;
+  const double c1 = first ? 1.0 : 4.0 / 3.0, c2 = first ? 0.0 : -1.0 / 3.0;
+  const double adt = alpha * dt;
+  const double* Um1 = first ? nullptr : Unm1;
+  // reference residual ||G(U^n)||: the same absolute target for every predictor
+  {
+    PhaseTimer t(st, &stats->t_residual_ms);
+    rc = ldg_residual(h, Un, w.R, st);
+    if (rc) return rc;
+    k_bdf_residual<<<grid_for(n), 256, 0, st>>>(w.G, Un, Un, Um1, w.R, c1, c2, adt, n);
+    count_launch();
+  }
+  rc = norm2(h, w.G, &stats->res0, w, st);
+  if (rc) return rc;
+  const double target = o->rtol * stats->res0;
+  if (o->predictor == LDG_PRED_EXTRAP) k_extrap<<<grid_for(n), 256, 0, st>>>(U, Un, Um1, n);
+  count_launch();
+  // Jacobian state carried across calls; a mode or dt change forces a rebuild
+  bool rebuild = o->force_rebuild || !h->Jn || !h->Pn || h->jac_mode != mode;
+  if (h->jac_mode != mode && h->Jn) {
+    ldg_jac_destroy(h->Jn);
+    ldg_pc_destroy(h->Pn);
+    h->Jn = nullptr;
+    h->Pn = nullptr;
+  }
+  bool pc_stale = h->pc_adt != adt;
+  double gprev = 0.0;
+  for (int it = 0; it <= o->max_newton; ++it) {
+    double gn = 0.0;
+    {
+      PhaseTimer t(st, &stats->t_residual_ms);
+      rc = ldg_residual(h, U, w.R, st);
+      if (rc) return rc;
+      k_bdf_residual<<<grid_for(n), 256, 0, st>>>(w.G, U, Un, Um1, w.R, c1, c2, adt, n);
+      count_launch();
+    }
+    rc = norm2(h, w.G, &gn, w, st);
+    if (rc) return rc;
+    if (it == 0) stats->res_pred = gn;
+    stats->res_final = gn;
+    if (gn <= target) return LDG_OK;
+    if (it == o->max_newton) break;
+    if (it > 0 && gn > 0.5 * gprev) rebuild = true;  // slow convergence: refresh the Jacobian
+    gprev = gn;
+    if (rebuild || h->jac_age > o->reuse) {
+      {
+        PhaseTimer t(st, &stats->t_jacobian_ms);
+        rc = ldg_jacobian(h, U, vprec, &h->Jn, st);
+        if (rc) return rc;
+      }
+      pc_stale = true;
+      h->jac_age = 0;
+      h->jac_mode = mode;
+      stats->jac_builds++;
+      rebuild = false;
+    }
+    if (pc_stale) {
+      PhaseTimer t(st, &stats->t_precond_ms);
+      rc = ldg_precond(h, h->Jn, 1.0, -adt, &h->Pn, st);
+      if (rc) return rc;
+      h->pc_adt = adt;
+      pc_stale = false;
+    }
+    // linear solve for delta with -G on the right
+    {
+      PhaseTimer t(st, &stats->t_linear_ms);
+      int its = 0;
+      double rel = 0;
+      if (mode == LDG_MODE_FP64) {
+        k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
+        count_launch();
+        rc = gmres<double>(h, vprec, w.r64, w.delta, adt, o->gmres_tol, o->restart, w, &its, &rel, st);
+        if (rc) return rc;
+        stats->gmres_its += its;
+      } else {
+        // FP64 iterative refinement around FP32 GMRES
+        LDG_CUDA_TRY(cudaMemsetAsync(w.delta, 0, n * sizeof(double), st));
+        k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
+        count_launch();
+        const int sweeps = o->max_refine < 1 ? 1 : o->max_refine;
+        for (int s = 0; s < sweeps; ++s) {
+          if (s > 0) {
+            // r = -G - (I - adt A) delta, FP64 vectors with the FP32 matrix
+            if (launch_jacvec(h, h->Jn, 1.0, -adt, w.delta, w.tmp64, LDG_PREC_FP64, st) != cudaSuccess)
+              return LDG_ERR_CUDA;
+            k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
+            count_launch();
+            k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(w.r64, w.tmp64, -1.0, n);
+            count_launch();
+            double rn = 0, gnn = gn;
+            rc = norm2(h, w.r64, &rn, w, st);
+            if (rc) return rc;
+            if (rn <= o->gmres_tol * gnn) break;
+          }
+          double rn = 0;
+          rc = norm2(h, w.r64, &rn, w, st);
+          if (rc) return rc;
+          if (rn == 0.0) break;
+          // the scaled residual goes to the last basis slot, which GMRES reads
+          // only before it starts writing the basis
+          float* rb = (float*)w.Vb + (int64_t)o->restart * n;
+          k_scale_to<double, float><<<grid_for(n), 256, 0, st>>>(rb, w.r64, 1.0 / rn, n);
+          count_launch();
+          float* xf = (float*)w.tmp64;  // the FP32 correction fits in the FP64 temporary
+          rc = gmres<float>(h, vprec, rb, xf, adt, o->gmres_tol, o->restart, w, &its, &rel, st);
+          if (rc) return rc;
+          stats->gmres_its += its;
+          stats->refine_sweeps++;
+          k_axpy_d<float><<<grid_for(n), 256, 0, st>>>(w.delta, xf, rn, n);
+          count_launch();
+        }
+      }
+    }
+    k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(U, w.delta, 1.0, n);
+    count_launch();
+    stats->newton_its++;
+    h->jac_age++;
+  }
+  return LDG_ERR_NEWTON_MAXIT;
+}

@@ -84,6 +84,7 @@ _SIGS = {
     "ldg_precond_apply": [_P, _P, _P, _P, _I, _P],
     "ldg_pc_destroy": [_P],
     "ldg_pc_export": [_P, _P],
+    "ldg_launch_count": [C.POINTER(C.c_longlong)],
     "ldg_newton_step": [_P, _P, _P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t),
                         C.POINTER(ldg_step_stats_t), _P],
 }
@@ -213,6 +214,22 @@ class Handle:
     def shape(self):
         return (self.E, self.nc, self.npe)
 
+    @property
+    def nlines(self):
+        return self.E * self.D * self.nl
+
+    @property
+    def ntiles(self):
+        return (self.nlines + 31) // 32
+
+    @property
+    def nk11(self):
+        return self.k11_len // self.nlines
+
+    @property
+    def nk12(self):
+        return self.k12_len // self.nlines
+
 
 def ldg_setup(mesh, eq):
     m = _Marshal(mesh, eq)
@@ -332,3 +349,9 @@ def ldg_newton_step(h, U_next, U_n, U_nm1, U_nm2, dt, opts, stream=None):
                                  float(dt), C.byref(opts), C.byref(st), _stream(stream)),
            "ldg_newton_step")
     return st.as_dict()
+
+
+def ldg_launch_count():
+    v = C.c_longlong()
+    _check(lib().ldg_launch_count(C.byref(v)), "ldg_launch_count")
+    return v.value

@@ -1,0 +1,285 @@
+"""GPU parity of the line-sparse Jacobian (K11, K12, K21), the split
+Jacobian-vector product, the element-block ILU(0) preconditioner and the
+Newton-BDF2 step against the oracle (complex-step Jacobians, textbook
+ILU(0) and GMRES). Tolerances: 1e-5 relative per block row for FP32 values
+(the benchmark spec), 1e-11 for the FP64 build; integer structure bit-exact."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1204_1533_gb300 import inputs as I
+from oracle import jacobian as JAC
+from oracle import solvers as S
+from oracle.mesh import line_nodes
+from oracle.residual import Discretization, full_residual, gradient
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1204_1533_gb300 import build, ldg
+    build.build()
+    return ldg
+
+
+def ns(mu=0.05):
+    return {"kind": "ns", "gamma": 1.4, "flux": "roe", "mu": mu, "Pr": 0.72}
+
+
+EULER = {"kind": "euler", "gamma": 1.4, "flux": "roe"}
+
+
+def _fs(m, nc, v=(0.5, -0.2, 0.3), p=2.0):
+    D = m["D"]
+    E, npe = m["nodes"].shape[:2]
+    U = np.zeros((E, nc, npe))
+    U[:, 0] = 1.0
+    for a in range(D):
+        U[:, 1 + a] = v[a]
+    U[:, D + 1] = p / 0.4 + 0.5 * sum(x * x for x in v[:D])
+    return U
+
+
+def _case(name):
+    if name == "euler2d_p3":
+        m = I.reorient(I.vortex_mesh(4, 3, perturb=0.15))[0]
+        return m, EULER, I.smooth_perturbation(m, I.vortex_state(m), 0.05, periods=[10, 10]), None
+    if name == "lf2d_p2":
+        m = I.vortex_mesh(3, 2, perturb=0.15)
+        return m, dict(EULER, flux="lf"), I.smooth_perturbation(m, I.vortex_state(m), 0.05), None
+    if name == "ns2d_p2":
+        m = I.reorient(I.structured_mesh((3, 3), 2, (0, 0), (1, 1), (True, True), perturb=0.1))[0]
+        return m, ns(), I.smooth_perturbation(m, _fs(m, 4), 0.1, periods=[1, 1]), None
+    if name == "ns3d_p2":
+        m = I.structured_mesh((3, 3, 3), 2, (0,) * 3, (2 * math.pi,) * 3, (True,) * 3, perturb=0.1)
+        return m, ns(0.02), I.smooth_perturbation(m, I.tgv_state(m, mach=0.3), 0.05), None
+    if name == "poisson_p3":
+        m = I.poisson_square_mesh(4, 3)
+        gD = np.zeros((16, 1, 16))
+        eq = {"kind": "poisson", "bc": {0: "dirichlet"}, "gD": gD, "source": I.poisson_source(m)}
+        return m, eq, I.poisson_exact(m) + 0.1, gD
+    raise KeyError(name)
+
+
+def _oeq(eq):
+    o = {k: v for k, v in eq.items() if k not in ("gD", "source")}
+    o.setdefault("bc", {0: "dirichlet"})
+    return o
+
+
+def _sparse_from_export(disc, K11, K12, K21):
+    """Scatter the library's line-block arrays into sparse matrices with the
+    oracle's flat index conventions (layout documented in include/ldg.h)."""
+    D, p, nc, npe, nl, E = disc.D, disc.p, disc.nc, disc.npe, disc.nl, disc.E
+    n = p + 1
+    nbr, sw = disc.conn.nbr, disc.S
+    r11, c11, v11, r12, c12, v12, r21, c21, v21 = ([] for _ in range(9))
+    for e in range(E):
+        for d in range(D):
+            for l in range(nl):
+                Lx = (e * D + d) * nl + l
+                ln = line_nodes(D, p, d, l)
+                for i in range(n):
+                    for c in range(nc):
+                        row = (e * nc + c) * npe + ln[i]
+                        for j in range(n):
+                            for cp in range(nc):
+                                r11.append(row)
+                                c11.append((e * nc + cp) * npe + ln[j])
+                                v11.append(K11[((i * n + j) * nc + c) * nc + cp, Lx])
+                        for end in range(2):
+                            g = nbr[e, d, l, end]
+                            if g < 0:
+                                continue
+                            eo, ao = divmod(int(g), npe)
+                            for cp in range(nc):
+                                r11.append(row)
+                                c11.append((eo * nc + cp) * npe + ao)
+                                v11.append(K11[n * n * nc * nc + ((end * n + i) * nc + c) * nc + cp, Lx])
+                        if K12 is None:
+                            continue
+                        ncd = nc * D
+                        for j in range(n):
+                            for cp in range(nc):
+                                for b in range(D):
+                                    r12.append(row)
+                                    c12.append(((e * nc + cp) * D + b) * npe + ln[j])
+                                    v12.append(K12[((i * n + j) * nc + c) * ncd + cp * D + b, Lx])
+                        for end in range(2):
+                            g = nbr[e, d, l, end]
+                            if g < 0 or sw[e, d, end] != 1:
+                                continue
+                            eo, ao = divmod(int(g), npe)
+                            for cp in range(nc):
+                                for b in range(D):
+                                    r12.append(row)
+                                    c12.append(((eo * nc + cp) * D + b) * npe + ao)
+                                    v12.append(K12[n * n * nc * ncd + (i * nc + c) * ncd + cp * D + b, Lx])
+                    if K21 is None:
+                        continue
+                    for c in range(nc):
+                        for b in range(D):
+                            row = ((e * nc + c) * D + b) * npe + ln[i]
+                            for j in range(n):
+                                r21.append(row)
+                                c21.append((e * nc + c) * npe + ln[j])
+                                v21.append(K21[(i * n + j) * D + b, Lx])
+                            for end in range(2):
+                                g = nbr[e, d, l, end]
+                                if g < 0 or sw[e, d, end] != -1:
+                                    continue
+                                eo, ao = divmod(int(g), npe)
+                                r21.append(row)
+                                c21.append((eo * nc + c) * npe + ao)
+                                v21.append(K21[n * n * D + i * D + b, Lx])
+    N, NQ = E * nc * npe, E * nc * D * npe
+    out = [sp.csr_matrix((np.array(v11, np.float64), (r11, c11)), shape=(N, N))]
+    if K12 is not None:
+        out.append(sp.csr_matrix((np.array(v12, np.float64), (r12, c12)), shape=(N, NQ)))
+        out.append(sp.csr_matrix((np.array(v21, np.float64), (r21, c21)), shape=(NQ, N)))
+    else:
+        out += [None, None]
+    return out
+
+
+def _row_rel(A, B):
+    """max over rows of max|A_r - B_r| / max|B_r| (rows with B_r = 0 use 1)."""
+    A, B = sp.csr_matrix(A), sp.csr_matrix(B)
+    Dm = abs(A - B).max(axis=1).toarray().ravel()
+    Bm = abs(B).max(axis=1).toarray().ravel()
+    Bm[Bm == 0] = 1.0
+    return float((Dm / Bm).max())
+
+
+def _gpu_jac(L, h, U, prec):
+    import torch
+    Ut = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    J = L.ldg_jacobian(h, Ut, prec)
+    torch.cuda.synchronize()
+    return J
+
+
+@pytest.mark.parametrize("name", ["euler2d_p3", "lf2d_p2", "ns2d_p2", "ns3d_p2", "poisson_p3"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_jacobian_matches_complex_step(L, name, prec):
+    m, eq, U, gD = _case(name)
+    disc = Discretization(m, _oeq(eq))
+    Q = gradient(disc, U, gD) if disc.eq["kind"] in ("ns", "poisson") else None
+    src = eq.get("source")
+    h = L.ldg_setup(m, eq)
+    J = _gpu_jac(L, h, U, prec)
+    K11, K12, K21 = _sparse_from_export(disc, *L.ldg_jac_export(J))
+    tol = 1e-5 if prec == 0 else 1e-11
+    assert _row_rel(K11, JAC.K11(disc, U, Q, gD, src)) < tol
+    if K12 is not None:
+        assert _row_rel(K12, JAC.K12(disc, U, Q, gD, src)) < tol
+        assert _row_rel(K21, JAC.K21(disc, gD)) < tol
+
+
+def test_line_block_row_counts(L):
+    # structural: every K11 row of the line-block format stores D(p+1) n_c
+    # in-line entries (diagonal once per direction) plus 2 D n_c face entries
+    m, eq, U, _ = _case("ns3d_p2")
+    h = L.ldg_setup(m, eq)
+    J = _gpu_jac(L, h, U, 0)
+    K11, K12, K21 = L.ldg_jac_export(J)
+    n, nc, D = 3, 5, 3
+    assert K11.shape[0] == (n * n + 2 * n) * nc * nc
+    per_row = (D * n * nc + 2 * D * nc)
+    assert K11.shape[0] * K11.shape[1] == h.ndof * per_row
+
+
+@pytest.mark.parametrize("name", ["euler2d_p3", "ns2d_p2", "ns3d_p2", "poisson_p3"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_split_jacvec(L, name, prec):
+    import torch
+    m, eq, U, gD = _case(name)
+    disc = Discretization(m, _oeq(eq))
+    Q = gradient(disc, U, gD) if disc.eq["kind"] in ("ns", "poisson") else None
+    K11o = JAC.K11(disc, U, Q, gD)
+    K12o = JAC.K12(disc, U, Q, gD) if Q is not None else None
+    K21o = JAC.K21(disc, gD) if Q is not None else None
+    x = np.random.default_rng(7).standard_normal(U.size)
+    shift, scale = 1.0, -0.37
+    yo = S.split_matvec(K11o, K12o, K21o, x, shift, scale)
+    h = L.ldg_setup(m, eq)
+    J = _gpu_jac(L, h, U, prec)
+    dt = torch.float32 if prec == 0 else torch.float64
+    xt = torch.from_numpy(x).to(dt).cuda()
+    y = torch.empty_like(xt)
+    L.ldg_jacvec(h, J, shift, scale, xt, y, prec)
+    torch.cuda.synchronize()
+    err = np.abs(y.double().cpu().numpy() - yo).max() / np.abs(yo).max()
+    assert err < (2e-5 if prec == 0 else 1e-11), err
+    if prec == 0:
+        # FP64 vectors against the FP32 matrix (the refinement residual)
+        y64 = torch.empty(x.size, dtype=torch.float64, device="cuda")
+        L.ldg_jacvec(h, J, shift, scale, torch.from_numpy(x).cuda(), y64, 1)
+        assert np.abs(y64.cpu().numpy() - yo).max() / np.abs(yo).max() < 2e-5
+
+
+@pytest.mark.parametrize("name", ["euler2d_p3", "ns2d_p2", "ns3d_p2", "poisson_p3"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_preconditioner_factors_and_apply(L, name, prec):
+    import torch
+    m, eq, U, gD = _case(name)
+    disc = Discretization(m, _oeq(eq))
+    Q = gradient(disc, U, gD) if disc.eq["kind"] in ("ns", "poisson") else None
+    A = JAC.K11(disc, U, Q, gD)
+    if Q is not None:
+        A = A + JAC.K12(disc, U, Q, gD) @ JAC.K21(disc, gD)
+    shift, scale = 1.0, -0.3
+    pat = S.line_pattern(disc.D, disc.p)
+    Fo = S.ilu0(S.masked_blocks(disc, A, shift, scale), pat)
+    h = L.ldg_setup(m, eq)
+    J = _gpu_jac(L, h, U, prec)
+    P = L.ldg_precond(h, J, shift, scale)
+    Fg = L.ldg_pc_export(P, prec).astype(np.float64)
+    # scatter the oracle's dense element blocks into the pattern layout
+    Fo_p = np.stack([Fo[:, i, pat[i]] for i in range(disc.npe)], axis=1)
+    tol = 1e-5 if prec == 0 else 1e-10
+    scale_r = np.abs(Fo_p).max(axis=(2, 3, 4), keepdims=True)
+    assert (np.abs(Fg - Fo_p) / scale_r).max() < tol
+    r = np.random.default_rng(3).standard_normal(U.shape)
+    zo = S.ilu_apply(Fo, pat, r)
+    dt = torch.float32 if prec == 0 else torch.float64
+    rt = torch.from_numpy(r).to(dt).cuda()
+    z = torch.empty_like(rt)
+    L.ldg_precond_apply(h, P, rt, z, prec)
+    torch.cuda.synchronize()
+    assert np.abs(z.double().cpu().numpy() - zo).max() / np.abs(zo).max() < (1e-4 if prec == 0 else 1e-10)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", ["euler2d_p3", "ns2d_p2"])
+def test_newton_bdf2_step(L, mode, name):
+    """One BDF1 then one BDF2 level to ||G|| <= 1e-8 ||G(U^n)||, compared with
+    the oracle's Newton solution of the same stage equation solved to 1e-12."""
+    import torch
+    m, eq, U0, _ = _case(name)
+    disc = Discretization(m, _oeq(eq))
+    dt = 0.05 if name.startswith("euler") else 0.01
+    F = lambda X: full_residual(disc, X)
+
+    def jac(X):
+        if disc.eq["kind"] == "ns":
+            Qx = gradient(disc, X)
+            return JAC.K11(disc, X, Qx), JAC.K12(disc, X, Qx), JAC.K21(disc)
+        return JAC.K11(disc, X), None, None
+    U1o, _ = S.newton_bdf2(F, jac, U0, None, dt, first=True, rtol=1e-12, gmres_tol=1e-10, restart=400, reuse=1)
+    U2o, _ = S.newton_bdf2(F, jac, U1o, U0, dt, first=False, rtol=1e-12, gmres_tol=1e-10, restart=400, reuse=1)
+    h = L.ldg_setup(m, eq)
+    Un = torch.from_numpy(U0).cuda()
+    U1 = torch.empty_like(Un)
+    st1 = L.ldg_newton_step(h, U1, Un, None, None, dt, L.solver_opts(mode=mode, first_step=True))
+    U2 = torch.empty_like(Un)
+    st2 = L.ldg_newton_step(h, U2, U1, Un, None, dt, L.solver_opts(mode=mode, force_rebuild=False))
+    for st in (st1, st2):
+        assert st["res_final"] <= 1e-8 * st["res0"]
+        assert st["newton_its"] <= 10
+    d1 = np.abs(U1.cpu().numpy() - U1o).max() / np.abs(U1o).max()
+    d2 = np.abs(U2.cpu().numpy() - U2o).max() / np.abs(U2o).max()
+    assert d1 < 1e-7 and d2 < 1e-7, (d1, d2)

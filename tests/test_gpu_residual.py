@@ -163,14 +163,24 @@ def test_free_stream_and_conservation_on_gpu(L):
 
 
 def test_full_size_vortex_64x64_p4(L):
-    """The 64x64, p=4 vortex workload at full size, every output checked."""
+    """The 64x64, p=4 vortex workload at full size, every output checked.
+
+    At this resolution the residual cancels summands about 500 times larger
+    than R (p^2 |F| |n| / (J |R|)), and any float64 evaluation sits about
+    1e-12 relative from the exact value: the float64 oracle itself is
+    1.0e-12 away from its extended-precision evaluation. The bound is
+    therefore 1e-12 relative, or, where float64 cannot resolve that, no worse
+    than twice the float64 oracle's own distance from the reference."""
     import torch
     m = I.vortex_mesh(64, 4)
     U = I.smooth_perturbation(m, I.vortex_state(m), 0.05)
-    Ro = _ref_residual(Discretization(m, EULER), U)
+    disc = Discretization(m, EULER)
+    Ro = _ref_residual(disc, U)
+    floor64 = np.abs(full_residual(disc, U) - Ro).max()
     h = L.ldg_setup(m, EULER)
     Ut = torch.from_numpy(U).cuda()
     R = torch.empty_like(Ut)
     L.ldg_residual(h, Ut, R)
     torch.cuda.synchronize()
-    assert np.abs(R.cpu().numpy() - Ro).max() <= RTOL * np.abs(Ro).max()
+    err = np.abs(R.cpu().numpy() - Ro).max()
+    assert err <= max(RTOL * np.abs(Ro).max(), 2.0 * floor64), (err, floor64)
