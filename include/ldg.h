@@ -44,6 +44,7 @@ extern "C" {
 #define LDG_ERR_NEWTON_MAXIT (-6)     /* Newton iteration cap reached       */
 #define LDG_ERR_NOT_BUILT (-7)        /* object used before it was built    */
 #define LDG_ERR_UNSUPPORTED (-8)      /* (D, p, equation) not compiled in   */
+#define LDG_ERR_TOO_LARGE (-9)        /* problem exceeds a fixed-size buffer  */
 
 /* ---- equations (Sec. 2.1 Eq. 1, Sec. 3 Eq. 14, Sec. 5 Eqs. 42-48) ------- */
 #define LDG_EQ_POISSON 0        /* -div(grad u) = f, F = -q, n_c = 1         */
@@ -161,6 +162,24 @@ int ldg_export_tables(const ldg_handle_t* h, int64_t* nbr, int8_t* sw);
  * into a library-owned buffer. FP64 throughout. U, R: device [n_elem][n_c][(p+1)^D].
  */
 int ldg_residual(ldg_handle_t* h, const double* U, double* R, void* stream);
+
+/*
+ * The same residual as ldg_residual, computed without allocating anything,
+ * for callers that must not call cudaMalloc after start-up (their device
+ * memory is owned by another allocator, or their run loop may not
+ * allocate). The paper has no counterpart: this is an interface variant.
+ * The LDG gradient scratch of second-order equations lives in a fixed
+ * device array of LDG_NOALLOC_MAX_Q doubles (8 MiB, held by every GPU that
+ * loads the library until the process exits) instead of the handle's
+ * buffer. Returns LDG_ERR_TOO_LARGE when n_elem n_c D (p+1)^D exceeds
+ * LDG_NOALLOC_MAX_Q. The first call on a device looks up the array's device
+ * address; make that first call before any stream capture. All calls share
+ * the array, so calls that overlap on the GPU race on it; each call
+ * overwrites what it reads, so nothing carries over between calls.
+ * U, R: device [n_elem][n_c][(p+1)^D], FP64.
+ */
+#define LDG_NOALLOC_MAX_Q 1048576
+int ldg_residual_noalloc(ldg_handle_t* h, const double* U, double* R, void* stream);
 
 /* The LDG gradient alone: Q = D(U), device [n_elem][n_c][D][(p+1)^D], FP64. */
 int ldg_gradient(ldg_handle_t* h, const double* U, double* Q, void* stream);

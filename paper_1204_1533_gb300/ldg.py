@@ -23,7 +23,7 @@ MODE_FP64, MODE_MIXED = 0, 1
 PRED_EXTRAP, PRED_GIVEN = 0, 1
 ERRORS = {-1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_MESH", -4: "LDG_ERR_NONFINITE",
           -5: "LDG_ERR_GMRES_BREAKDOWN", -6: "LDG_ERR_NEWTON_MAXIT", -7: "LDG_ERR_NOT_BUILT",
-          -8: "LDG_ERR_UNSUPPORTED"}
+          -8: "LDG_ERR_UNSUPPORTED", -9: "LDG_ERR_TOO_LARGE"}
 
 
 class LdgError(RuntimeError):
@@ -85,6 +85,7 @@ _SIGS = {
     "ldg_pc_destroy": [_P],
     "ldg_pc_export": [_P, _P],
     "ldg_launch_count": [C.POINTER(C.c_longlong)],
+    "ldg_residual_noalloc": [_P, _P, _P, _P],
     "ldg_newton_step": [_P, _P, _P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t),
                         C.POINTER(ldg_step_stats_t), _P],
 }
@@ -355,3 +356,10 @@ def ldg_launch_count():
     v = C.c_longlong()
     _check(lib().ldg_launch_count(C.byref(v)), "ldg_launch_count")
     return v.value
+
+
+def ldg_residual_noalloc(h, U, R, stream=None):
+    """ldg_residual without allocation (fixed device scratch; see ldg.h)."""
+    _check(lib().ldg_residual_noalloc(h.ptr, _dptr(U), _dptr(R), _stream(stream)),
+           "ldg_residual_noalloc")
+    return R
