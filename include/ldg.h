@@ -299,6 +299,61 @@ int ldg_newton_step(ldg_handle_t* h, double* U_next, const double* U_n, const do
                     const double* U_nm2, double dt, const ldg_solver_opts_t* opts,
                     ldg_step_stats_t* stats, void* stream);
 
+/* ---- learned Newton predictor (not in the paper) ------------------------
+ * A line-local MLP n_in -> 128 -> 128 -> 128 -> n_out with GELU (tanh form)
+ * predicts, for every line of reference direction 1, the correction to the
+ * linear extrapolation 2 U^n - U^{n-1} of the next BDF level. Features per
+ * line: [u^n, u^n - u^{n-1}, u^{n-1} - u^{n-2}] over the line's nodes
+ * (index (level (p+1) + t) n_c + c) and the D x D deformation gradient
+ * averaged over the line divided by the line average of J^(1/D), each
+ * standardised; n_in = 3 (p+1) n_c + D^2 <= 96, n_out = (p+1) n_c <= 32.
+ * Weights are FP32 masters with BF16 copies; products run on BF16 tensor
+ * cores with FP32 accumulation. Parameters are exchanged as one flat vector
+ * W1 [n_in][128], b1, W2 [128][128], b2, W3 [128][128], b3, W4 [128][n_out],
+ * b4. Feature rows X are BF16 [M][96] (device), targets and outputs FP32
+ * [M][n_out] (device), in units of the per-output scale.
+ */
+typedef struct ldg_mlp ldg_mlp_t;
+
+/* Create a network with zero weights (set them with ldg_mlp_params). */
+int ldg_mlp_create(int32_t n_in, int32_t n_out, ldg_mlp_t** out);
+int ldg_mlp_destroy(ldg_mlp_t* m);
+
+/* Get (set = 0) or set (set = 1) the FP32 master parameters through a host
+ * FP64 array; setting resets the Adam state. Synchronous. */
+int ldg_mlp_params(ldg_mlp_t* m, double* theta, int32_t set);
+
+/* Standardisation of the features (mean, std; host [n_in]) and the output
+ * scale (host [n_out]). */
+int ldg_mlp_set_scaling(ldg_mlp_t* m, const double* in_mean, const double* in_std,
+                        const double* out_scale);
+
+/* Y = MLP(X) for M rows. */
+int ldg_mlp_forward(ldg_mlp_t* m, const void* X, int64_t M, float* Y, void* stream);
+
+/* Gradient of the mean squared error mean((Y - T)^2) over all M n_out
+ * outputs: grad device [n_params], loss device scalar (may be NULL). */
+int ldg_mlp_grad(ldg_mlp_t* m, const void* X, const float* T, int64_t M, float* grad, float* loss,
+                 void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the gradient of
+ * ldg_mlp_grad's loss; loss device scalar or NULL. */
+int ldg_mlp_train_step(ldg_mlp_t* m, const void* X, const float* T, int64_t M, double lr, float* loss,
+                       void* stream);
+
+/* Standardised features of every direction-1 line of U^n, U^{n-1}, U^{n-2}
+ * (device FP64 nodal arrays) into X (device BF16 [n_elem (p+1)^(D-1)][96]). */
+int ldg_line_features(ldg_handle_t* h, const ldg_mlp_t* m, const double* Un, const double* Unm1,
+                      const double* Unm2, void* X, void* stream);
+
+/* Scaled targets (U^{n+1} - 2 U^n + U^{n-1}) / scale per line, FP32 [lines][n_out]. */
+int ldg_line_targets(ldg_handle_t* h, const ldg_mlp_t* m, const double* Unext, const double* Un,
+                     const double* Unm1, float* T, void* stream);
+
+/* U0 = 2 U^n - U^{n-1} + scale * MLP(features), device FP64 nodal array. */
+int ldg_mlp_predict(ldg_handle_t* h, ldg_mlp_t* m, const double* Un, const double* Unm1,
+                    const double* Unm2, double* U0, void* stream);
+
 /* Number of kernels the library has launched since it was loaded (a host
  * counter; for benchmarks that report launches per step). */
 int ldg_launch_count(long long* out);

@@ -82,6 +82,7 @@ struct ldg_handle {
   int16_t* lvl = nullptr;    // rows sorted by wavefront level (sum of indices) [npe]
   int32_t* lvl_ptr = nullptr; // level start offsets [D p + 2]
   bool has_wall = false;
+  float* linemet = nullptr;  // per direction-1 line: line-averaged G / h, [E nl][D D]
   // Newton-Krylov state kept across time steps (Jacobian re-use, Sec. 4.3)
   struct ldg_jac* Jn = nullptr;
   struct ldg_pc* Pn = nullptr;

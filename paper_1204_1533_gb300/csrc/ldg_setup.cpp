@@ -209,7 +209,7 @@ void face_corner_ids(const int64_t* verts, int D, int f, int64_t* out) {
 // handle without device buffers and ng/nend/invJ hold the metric terms.
 static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_handle_t** hp,
                       std::vector<double>& ng, std::vector<double>& nend,
-                      std::vector<double>& invJ) {
+                      std::vector<double>& invJ, std::vector<float>& linemet) {
   *hp = nullptr;
   const int D = mesh->D, p = mesh->p;
   const int64_t E = mesh->n_elem;
@@ -400,6 +400,7 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
       }
     }
   // ---- metric terms ------------------------------------------------------------
+  linemet.assign((size_t)E * nl * D * D, 0.0f);
   ng.assign((size_t)E * D * nl * nq * D, 0.0);
   nend.assign((size_t)E * D * nl * 2 * D, 0.0);
   invJ.assign((size_t)E * npe, 0.0);
@@ -444,6 +445,22 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
             Gn[a * 9 + x * 3 + b] = acc;
           }
         }
+    // predictor features: G averaged over each direction-1 line, over the
+    // line average of h = J^(1/D)
+    for (int l = 0; l < nl; ++l) {
+      ld gs[9] = {0}, hs = 0;
+      for (int t2 = 0; t2 < n; ++t2) {
+        const int a = line_node(D, p, 0, l, t2);
+        const ld* G = &Gn[a * 9];
+        const ld J = (D == 2) ? G[0] * G[4] - G[1] * G[3]
+                              : G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                                    G[2] * (G[3] * G[7] - G[4] * G[6]);
+        hs += std::pow(J > 0 ? J : (ld)0, (ld)1 / D);
+        for (int x = 0; x < D; ++x)
+          for (int b = 0; b < D; ++b) gs[x * D + b] += G[x * 3 + b];
+      }
+      for (int k = 0; k < D * D; ++k) linemet[((size_t)e * nl + l) * D * D + k] = (float)(gs[k] / hs);
+    }
     for (int a = 0; a < npe; ++a) {
       const ld* G = &Gn[a * 9];
       ld J;
@@ -498,8 +515,9 @@ extern "C" int ldg_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_
   if (!mesh || !eq || !out) return LDG_ERR_ARG;
   *out = nullptr;
   std::vector<double> ng, nend, invJ;
+  std::vector<float> linemet;
   ldg_handle_t* h = nullptr;
-  int rc = host_setup(mesh, eq, &h, ng, nend, invJ);
+  int rc = host_setup(mesh, eq, &h, ng, nend, invJ, linemet);
   if (rc != LDG_OK) return rc;
   const int D = h->D;
   // ---- upload ---------------------------------------------------------------
@@ -519,6 +537,7 @@ extern "C" int ldg_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_
   if (err == cudaSuccess && eq->source)
     err = up((void**)&h->src, eq->source, (size_t)h->ndof * sizeof(double));
   if (err == cudaSuccess) err = up((void**)&h->nbf, h->nbf_h.data(), h->nbf_h.size());
+  if (err == cudaSuccess) err = up((void**)&h->linemet, linemet.data(), linemet.size() * sizeof(float));
   if (err == cudaSuccess && h->viscous())
     err = cudaMalloc((void**)&h->Qbuf, (size_t)h->ndof * D * sizeof(double));
   if (err == cudaSuccess) {
@@ -570,8 +589,9 @@ extern "C" int ldg_setup_host(const ldg_mesh_t* mesh, const ldg_equations_t* eq,
                               int8_t* sw, double* ng, double* nend, double* invJ, double* tables) {
   if (!mesh || !eq) return LDG_ERR_ARG;
   std::vector<double> vng, vnend, vinvJ;
+  std::vector<float> vlm;
   ldg_handle_t* h = nullptr;
-  int rc = host_setup(mesh, eq, &h, vng, vnend, vinvJ);
+  int rc = host_setup(mesh, eq, &h, vng, vnend, vinvJ, vlm);
   if (rc != LDG_OK) return rc;
   if (nbr)
     for (size_t i = 0; i < h->nbr_h.size(); ++i) nbr[i] = h->nbr_h[i];
@@ -609,6 +629,7 @@ extern "C" int ldg_destroy(ldg_handle_t* h) {
   cudaFree(h->Qbuf);
   cudaFree(h->red);
   cudaFree(h->nbf);
+  cudaFree(h->linemet);
   cudaFree(h->pat);
   cudaFree(h->slot);
   cudaFree(h->lvl);

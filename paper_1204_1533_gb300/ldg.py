@@ -86,6 +86,16 @@ _SIGS = {
     "ldg_pc_export": [_P, _P],
     "ldg_launch_count": [C.POINTER(C.c_longlong)],
     "ldg_residual_noalloc": [_P, _P, _P, _P],
+    "ldg_mlp_create": [C.c_int32, C.c_int32, C.POINTER(_P)],
+    "ldg_mlp_destroy": [_P],
+    "ldg_mlp_params": [_P, _P, C.c_int32],
+    "ldg_mlp_set_scaling": [_P, _P, _P, _P],
+    "ldg_mlp_forward": [_P, _P, C.c_int64, _P, _P],
+    "ldg_mlp_grad": [_P, _P, _P, C.c_int64, _P, _P, _P],
+    "ldg_mlp_train_step": [_P, _P, _P, C.c_int64, C.c_double, _P, _P],
+    "ldg_line_features": [_P, _P, _P, _P, _P, _P, _P],
+    "ldg_line_targets": [_P, _P, _P, _P, _P, _P, _P],
+    "ldg_mlp_predict": [_P, _P, _P, _P, _P, _P, _P],
     "ldg_newton_step": [_P, _P, _P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t),
                         C.POINTER(ldg_step_stats_t), _P],
 }
@@ -363,3 +373,73 @@ def ldg_residual_noalloc(h, U, R, stream=None):
     _check(lib().ldg_residual_noalloc(h.ptr, _dptr(U), _dptr(R), _stream(stream)),
            "ldg_residual_noalloc")
     return R
+
+
+MLP_INP = 96
+
+
+class Mlp:
+    def __init__(self, ptr, n_in, n_out):
+        self.ptr, self.n_in, self.n_out = ptr, n_in, n_out
+        self.n_params = n_in * 128 + 128 + 2 * (128 * 128 + 128) + 128 * n_out + n_out
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.ldg_mlp_destroy(self.ptr)
+            self.ptr = None
+
+
+def ldg_mlp_create(n_in, n_out):
+    ptr = C.c_void_p()
+    _check(lib().ldg_mlp_create(int(n_in), int(n_out), C.byref(ptr)), "ldg_mlp_create")
+    return Mlp(ptr, n_in, n_out)
+
+
+def ldg_mlp_params(m, theta=None):
+    """Return the FP32 master parameters (as float64) or set them."""
+    if theta is None:
+        out = np.zeros(m.n_params)
+        _check(lib().ldg_mlp_params(m.ptr, _hptr(out), 0), "ldg_mlp_params")
+        return out
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    _check(lib().ldg_mlp_params(m.ptr, _hptr(th), 1), "ldg_mlp_params")
+    return th
+
+
+def ldg_mlp_set_scaling(m, in_mean, in_std, out_scale):
+    a, b, c = (np.ascontiguousarray(x, dtype=np.float64) for x in (in_mean, in_std, out_scale))
+    _check(lib().ldg_mlp_set_scaling(m.ptr, _hptr(a), _hptr(b), _hptr(c)), "ldg_mlp_set_scaling")
+
+
+def ldg_mlp_forward(m, X, Y, stream=None):
+    _check(lib().ldg_mlp_forward(m.ptr, _dptr(X), X.shape[0], _dptr(Y), _stream(stream)), "ldg_mlp_forward")
+    return Y
+
+
+def ldg_mlp_grad(m, X, T, grad, loss=None, stream=None):
+    _check(lib().ldg_mlp_grad(m.ptr, _dptr(X), _dptr(T), X.shape[0], _dptr(grad), _dptr(loss),
+                              _stream(stream)), "ldg_mlp_grad")
+    return grad
+
+
+def ldg_mlp_train_step(m, X, T, lr, loss=None, stream=None):
+    _check(lib().ldg_mlp_train_step(m.ptr, _dptr(X), _dptr(T), X.shape[0], float(lr), _dptr(loss),
+                                    _stream(stream)), "ldg_mlp_train_step")
+
+
+def ldg_line_features(h, m, Un, Unm1, Unm2, X, stream=None):
+    _check(lib().ldg_line_features(h.ptr, m.ptr, _dptr(Un), _dptr(Unm1), _dptr(Unm2), _dptr(X),
+                                   _stream(stream)), "ldg_line_features")
+    return X
+
+
+def ldg_line_targets(h, m, Unext, Un, Unm1, T, stream=None):
+    _check(lib().ldg_line_targets(h.ptr, m.ptr, _dptr(Unext), _dptr(Un), _dptr(Unm1), _dptr(T),
+                                  _stream(stream)), "ldg_line_targets")
+    return T
+
+
+def ldg_mlp_predict(h, m, Un, Unm1, Unm2, U0, stream=None):
+    _check(lib().ldg_mlp_predict(h.ptr, m.ptr, _dptr(Un), _dptr(Unm1), _dptr(Unm2), _dptr(U0),
+                                 _stream(stream)), "ldg_mlp_predict")
+    return U0

@@ -1,0 +1,165 @@
+"""GPU parity of the line-MLP predictor kernels against the FP64 oracle.
+
+The GPU runs BF16 weights and activations with FP32 accumulation; the
+oracle evaluates the same network in FP64 on the BF16-rounded weights and
+inputs, so the remaining differences come from BF16 rounding of the hidden
+activations: forward outputs and gradients are compared normwise at 2e-2
+relative, the FP32 Adam update at 1e-6, features at one BF16 rounding."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1204_1533_gb300 import inputs as I
+from oracle import mlp as M
+from oracle.rules import Rules
+
+pytestmark = pytest.mark.gpu
+
+INP = 96
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1204_1533_gb300 import build, ldg
+    build.build()
+    return ldg
+
+
+def bf16(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def _rand_problem(n_in=69, n_out=20, M_rows=300, seed=0):
+    rng = np.random.default_rng(seed)
+    theta = M.init_params(n_in, n_out, seed=seed)
+    theta += 0.05 * rng.standard_normal(theta.size)
+    X = rng.standard_normal((M_rows, n_in))
+    T = rng.standard_normal((M_rows, n_out)) * 0.5
+    return theta, X, T
+
+
+def _round_weights(theta, n_in, n_out):
+    """W's to BF16 (as the GPU stores them), biases stay FP32."""
+    parts = M.unpack(theta.copy(), n_in, n_out)
+    out = []
+    for W, b in parts:
+        out += [bf16(W).ravel(), np.asarray(b, np.float32).astype(np.float64)]
+    return np.concatenate(out)
+
+
+def _xt(X):
+    import torch
+    Xp = np.zeros((X.shape[0], INP), np.float32)
+    Xp[:, :X.shape[1]] = X
+    return torch.from_numpy(Xp).to(torch.bfloat16).cuda()
+
+
+def test_forward_matches_oracle(L):
+    import torch
+    n_in, n_out = 69, 20
+    theta, X, _ = _rand_problem()
+    m = L.ldg_mlp_create(n_in, n_out)
+    L.ldg_mlp_params(m, theta)
+    Y = torch.empty((X.shape[0], n_out), dtype=torch.float32, device="cuda")
+    L.ldg_mlp_forward(m, _xt(X), Y)
+    Yo, _ = M.forward(_round_weights(theta, n_in, n_out), bf16(X), n_out)
+    err = np.linalg.norm(Y.cpu().numpy() - Yo) / np.linalg.norm(Yo)
+    assert err < 2e-2, err
+    # FP32 master parameters round-trip exactly through the FP64 interface
+    assert np.array_equal(L.ldg_mlp_params(m), theta.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("rows", [300, 32, 7])
+def test_gradient_matches_oracle(L, rows):
+    import torch
+    n_in, n_out = 69, 20
+    theta, X, T = _rand_problem(M_rows=rows, seed=rows)
+    m = L.ldg_mlp_create(n_in, n_out)
+    L.ldg_mlp_params(m, theta)
+    g = torch.empty(m.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    L.ldg_mlp_grad(m, _xt(X), torch.from_numpy(T.astype(np.float32)).cuda(), g, loss)
+    lo, go = M.loss_and_grad(_round_weights(theta, n_in, n_out), bf16(X), T)
+    gg = g.cpu().numpy()
+    assert abs(loss.item() - lo) < 2e-2 * lo
+    off = 0
+    for a, b in M.layer_shapes(n_in, n_out):
+        for size in (a * b, b):
+            sl = slice(off, off + size)
+            err = np.linalg.norm(gg[sl] - go[sl]) / max(np.linalg.norm(go[sl]), 1e-30)
+            assert err < 2e-2, (a, b, size, err)
+            off += size
+
+
+def test_adam_step_matches_oracle(L):
+    import torch
+    n_in, n_out = 69, 20
+    theta, X, T = _rand_problem(seed=3)
+    m = L.ldg_mlp_create(n_in, n_out)
+    L.ldg_mlp_params(m, theta)
+    Xt, Tt = _xt(X), torch.from_numpy(T.astype(np.float32)).cuda()
+    g = torch.empty(m.n_params, dtype=torch.float32, device="cuda")
+    L.ldg_mlp_grad(m, Xt, Tt, g)
+    L.ldg_mlp_train_step(m, Xt, Tt, 1e-3)
+    th_new = L.ldg_mlp_params(m)
+    ref, _, _ = M.adam_update(theta.astype(np.float32).astype(np.float64), g.cpu().numpy().astype(np.float64),
+                              np.zeros(theta.size), np.zeros(theta.size), 1, 1e-3)
+    assert np.abs(th_new - ref).max() < 1e-6
+
+
+def test_training_reduces_loss(L):
+    import torch
+    rng = np.random.default_rng(9)
+    n_in, n_out, rows = 69, 20, 4096
+    A = rng.standard_normal((n_in, n_out)) / math.sqrt(n_in)
+    X = rng.standard_normal((rows, n_in))
+    T = np.tanh(X @ A)
+    m = L.ldg_mlp_create(n_in, n_out)
+    L.ldg_mlp_params(m, M.init_params(n_in, n_out, seed=2))
+    Xt, Tt = _xt(X), torch.from_numpy(T.astype(np.float32)).cuda()
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    L.ldg_mlp_train_step(m, Xt, Tt, 2e-3, loss)
+    l0 = loss.item()
+    for _ in range(400):
+        L.ldg_mlp_train_step(m, Xt, Tt, 2e-3, loss)
+    assert loss.item() < 0.05 * l0, (l0, loss.item())
+
+
+def test_line_features_targets_and_predict(L):
+    import torch
+    m_ = I.tgv_mesh(3, 3)
+    eq = {"kind": "ns", "gamma": 1.4, "mu": 1 / 1600, "Pr": 0.72}
+    h = L.ldg_setup(m_, eq)
+    rng = np.random.default_rng(5)
+    base = I.tgv_state(m_)
+    U = [base * (1 + 0.01 * rng.standard_normal(base.shape)) for _ in range(4)]
+    n_in, n_out = 69, 20
+    mlp = L.ldg_mlp_create(n_in, n_out)
+    Fo = np.concatenate([M.line_state_features(U[2], U[1], U[0], 3, 3),
+                         M.line_metric_features(m_, Rules(3, m_["s"]))], axis=1)
+    mean, std = Fo.mean(axis=0), Fo.std(axis=0) + 1e-3
+    oscale = np.full(n_out, 0.7)
+    L.ldg_mlp_set_scaling(mlp, mean, std, oscale)
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    nl1 = h.E * h.nl
+    X = torch.empty((nl1, INP), dtype=torch.bfloat16, device="cuda")
+    L.ldg_line_features(h, mlp, Ud[2], Ud[1], Ud[0], X)
+    Xg = X.float().cpu().numpy()
+    ref = (Fo - mean) / std
+    assert np.all(Xg[:, n_in:] == 0)
+    assert np.abs(Xg[:, :n_in] - bf16(ref)).max() <= 1e-2 * max(1.0, np.abs(ref).max())
+    T = torch.empty((nl1, n_out), dtype=torch.float32, device="cuda")
+    L.ldg_line_targets(h, mlp, Ud[3], Ud[2], Ud[1], T)
+    To = M.line_targets(U[3], U[2], U[1], 3, 3) / oscale
+    assert np.abs(T.cpu().numpy() - To).max() <= 1e-6 * np.abs(To).max()
+    # predict = extrapolation + scaled network output, scattered to the nodes
+    theta = M.init_params(n_in, n_out, seed=4)
+    L.ldg_mlp_params(mlp, theta)
+    U0 = torch.empty_like(Ud[0])
+    L.ldg_mlp_predict(h, mlp, Ud[2], Ud[1], Ud[0], U0)
+    Y = torch.empty((nl1, n_out), dtype=torch.float32, device="cuda")
+    L.ldg_mlp_forward(mlp, X, Y)
+    ref = M.scatter_correction(Y.cpu().numpy().astype(np.float64) * oscale, U[2], U[1], 3, 3)
+    assert np.abs(U0.cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
