@@ -257,6 +257,10 @@ int ldg_pc_export(const ldg_pc_t* P, void* factors);
 
 #define LDG_PRED_EXTRAP 0  /* U0 = 2 U^n - U^{n-1} (U^n on the first step)   */
 #define LDG_PRED_GIVEN 1   /* U0 = the caller's U_next on entry             */
+#define LDG_PRED_CHECKED 2 /* the caller's guess U1 judged by the BDF residual:
+                              U0 = extrapolation, the guess is U0 + b (U1 - U0)
+                              with b in [0,1] minimising the linearised
+                              ||G||; b = 0 falls back to extrapolation       */
 
 typedef struct {
   int32_t mode;          /* LDG_MODE_*                                        */
@@ -265,7 +269,9 @@ typedef struct {
   int32_t restart;       /* GMRES restart length (<= 64)                      */
   int32_t max_newton;    /* iteration cap                                      */
   int32_t reuse;         /* rebuild K, P when Newton its since rebuild > reuse */
-  int32_t max_refine;    /* FP64 iterative-refinement sweeps per linear solve */
+  int32_t max_refine;    /* GMRES cycles per linear solve, each restarted from
+                            the true FP64 residual (the FP64 refinement of the
+                            mixed mode; restarted GMRES in the FP64 mode)     */
   int32_t force_rebuild; /* 1: build K, P at the first Newton iteration       */
   double rtol;           /* ||G(U)||_2 <= rtol ||G(U^n)||_2                  */
   double gmres_tol;      /* relative tolerance of each linear solve           */
@@ -283,6 +289,8 @@ typedef struct {
   double t_jacobian_ms;
   double t_precond_ms;
   double t_linear_ms;
+  double res_extrap;     /* ||G|| of the extrapolation (LDG_PRED_CHECKED)     */
+  double pred_weight;    /* weight b of the caller's guess (LDG_PRED_CHECKED) */
 } ldg_step_stats_t;
 
 /*
@@ -357,6 +365,10 @@ int ldg_mlp_predict(ldg_handle_t* h, ldg_mlp_t* m, const double* Un, const doubl
 /* Number of kernels the library has launched since it was loaded (a host
  * counter; for benchmarks that report launches per step). */
 int ldg_launch_count(long long* out);
+
+/* Change the constant viscosity of a Navier-Stokes handle (for sweeps over
+ * Reynolds numbers); a retained Jacobian is marked stale. */
+int ldg_set_viscosity(ldg_handle_t* h, double mu);
 
 /* ||x||_2 of a device FP64 vector (synchronous; for drivers and tests). */
 int ldg_norm2(ldg_handle_t* h, const double* x, int64_t n, double* out, void* stream);

@@ -105,6 +105,12 @@ __global__ void k_bdf_residual(double* __restrict__ G, const double* __restrict_
   }
 }
 
+// U = b U + (1 - b) U0
+__global__ void k_blend(double* __restrict__ U, const double* __restrict__ U0, double b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    U[i] = b * U[i] + (1.0 - b) * U0[i];
+}
+
 __global__ void k_extrap(double* __restrict__ U, const double* __restrict__ Un, const double* __restrict__ Unm1,
                          int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -328,8 +334,44 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
   rc = norm2(h, w.G, &stats->res0, w, st);
   if (rc) return rc;
   const double target = o->rtol * stats->res0;
-  if (o->predictor == LDG_PRED_EXTRAP) k_extrap<<<grid_for(n), 256, 0, st>>>(U, Un, Um1, n);
-  count_launch();
+  if (o->predictor == LDG_PRED_EXTRAP) {
+    k_extrap<<<grid_for(n), 256, 0, st>>>(U, Un, Um1, n);
+    count_launch();
+  } else if (o->predictor == LDG_PRED_CHECKED) {
+    // judge the caller's guess U1 by the BDF residual against the
+    // extrapolation U0: with G0 = G(U0), G1 = G(U1) and the linear model
+    // G(U0 + b (U1 - U0)) = G0 + b (G1 - G0), take the b in [0, 1] that
+    // minimises its norm; b = 0 is the fallback to extrapolation
+    double g1 = 0.0, g0 = 0.0, g01 = 0.0;
+    {
+      PhaseTimer t(st, &stats->t_residual_ms);
+      rc = ldg_residual(h, U, w.R, st);
+      if (rc) return rc;
+      k_bdf_residual<<<grid_for(n), 256, 0, st>>>(w.r64, U, Un, Um1, w.R, c1, c2, adt, n);
+      count_launch();
+      k_extrap<<<grid_for(n), 256, 0, st>>>(w.U0, Un, Um1, n);
+      count_launch();
+      rc = ldg_residual(h, w.U0, w.R, st);
+      if (rc) return rc;
+      k_bdf_residual<<<grid_for(n), 256, 0, st>>>(w.G, w.U0, Un, Um1, w.R, c1, c2, adt, n);
+      count_launch();
+    }
+    rc = norm2(h, w.r64, &g1, w, st);
+    if (rc) return rc;
+    rc = norm2(h, w.G, &g0, w, st);
+    if (rc) return rc;
+    if (mdot<double>(w.G, 1, n, w.r64, w.part, w.hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
+    count_launch(2);
+    LDG_CUDA_TRY(cudaMemcpyAsync(&g01, w.hcol, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LDG_CUDA_TRY(cudaStreamSynchronize(st));
+    const double dd = g1 * g1 - 2.0 * g01 + g0 * g0;  // ||G1 - G0||^2
+    double b = (g1 <= g0) ? 1.0 : 0.0;
+    if (dd > 0.0) b = std::fmin(1.0, std::fmax(0.0, (g0 * g0 - g01) / dd));
+    stats->res_extrap = g0;
+    stats->pred_weight = b;
+    k_blend<<<grid_for(n), 256, 0, st>>>(U, w.U0, b, n);
+    count_launch();
+  }
   // Jacobian state carried across calls; a mode or dt change forces a rebuild
   bool rebuild = o->force_rebuild || !h->Jn || !h->Pn || h->jac_mode != mode;
   if (h->jac_mode != mode && h->Jn) {
@@ -376,54 +418,56 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
       h->pc_adt = adt;
       pc_stale = false;
     }
-    // linear solve for delta with -G on the right
+    // linear solve for delta with -G on the right: restarted GMRES cycles,
+    // each restarted from the true residual r = -G - (I - adt A) delta formed
+    // with FP64 vectors (in the mixed mode this is the FP64 iterative
+    // refinement around FP32 GMRES; in the FP64 mode a restarted GMRES)
     {
       PhaseTimer t(st, &stats->t_linear_ms);
-      int its = 0;
-      double rel = 0;
-      if (mode == LDG_MODE_FP64) {
-        k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
-        count_launch();
-        rc = gmres<double>(h, vprec, w.r64, w.delta, adt, o->gmres_tol, o->restart, w, &its, &rel, st);
+      LDG_CUDA_TRY(cudaMemsetAsync(w.delta, 0, n * sizeof(double), st));
+      k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
+      count_launch();
+      const int sweeps = o->max_refine < 1 ? 1 : o->max_refine;
+      for (int s = 0; s < sweeps; ++s) {
+        if (s > 0) {
+          if (launch_jacvec(h, h->Jn, 1.0, -adt, w.delta, w.tmp64, LDG_PREC_FP64, st) != cudaSuccess)
+            return LDG_ERR_CUDA;
+          k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
+          count_launch();
+          k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(w.r64, w.tmp64, -1.0, n);
+          count_launch();
+        }
+        double rn = 0;
+        rc = norm2(h, w.r64, &rn, w, st);
         if (rc) return rc;
-        stats->gmres_its += its;
-      } else {
-        // FP64 iterative refinement around FP32 GMRES
-        LDG_CUDA_TRY(cudaMemsetAsync(w.delta, 0, n * sizeof(double), st));
-        k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
-        count_launch();
-        const int sweeps = o->max_refine < 1 ? 1 : o->max_refine;
-        for (int s = 0; s < sweeps; ++s) {
-          if (s > 0) {
-            // r = -G - (I - adt A) delta, FP64 vectors with the FP32 matrix
-            if (launch_jacvec(h, h->Jn, 1.0, -adt, w.delta, w.tmp64, LDG_PREC_FP64, st) != cudaSuccess)
-              return LDG_ERR_CUDA;
-            k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
-            count_launch();
-            k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(w.r64, w.tmp64, -1.0, n);
-            count_launch();
-            double rn = 0, gnn = gn;
-            rc = norm2(h, w.r64, &rn, w, st);
-            if (rc) return rc;
-            if (rn <= o->gmres_tol * gnn) break;
-          }
-          double rn = 0;
-          rc = norm2(h, w.r64, &rn, w, st);
+        if (rn <= o->gmres_tol * gn || rn == 0.0) break;
+        // relative tolerance of this cycle so that it reaches gmres_tol ||G||
+        const double tol = o->gmres_tol * gn / rn;
+        int its = 0;
+        double rel = 0;
+        if (mode == LDG_MODE_FP64) {
+          double* rb = (double*)w.Vb + (int64_t)o->restart * n;
+          k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(rb, w.r64, 1.0 / rn, n);
+          count_launch();
+          double* xe = w.tmp64;
+          rc = gmres<double>(h, vprec, rb, xe, adt, tol, o->restart, w, &its, &rel, st);
           if (rc) return rc;
-          if (rn == 0.0) break;
+          k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(w.delta, xe, rn, n);
+          count_launch();
+        } else {
           // the scaled residual goes to the last basis slot, which GMRES reads
           // only before it starts writing the basis
           float* rb = (float*)w.Vb + (int64_t)o->restart * n;
           k_scale_to<double, float><<<grid_for(n), 256, 0, st>>>(rb, w.r64, 1.0 / rn, n);
           count_launch();
           float* xf = (float*)w.tmp64;  // the FP32 correction fits in the FP64 temporary
-          rc = gmres<float>(h, vprec, rb, xf, adt, o->gmres_tol, o->restart, w, &its, &rel, st);
+          rc = gmres<float>(h, vprec, rb, xf, adt, tol, o->restart, w, &its, &rel, st);
           if (rc) return rc;
-          stats->gmres_its += its;
-          stats->refine_sweeps++;
           k_axpy_d<float><<<grid_for(n), 256, 0, st>>>(w.delta, xf, rn, n);
           count_launch();
         }
+        stats->gmres_its += its;
+        stats->refine_sweeps++;
       }
     }
     k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(U, w.delta, 1.0, n);
@@ -432,4 +476,11 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
     h->jac_age++;
   }
   return LDG_ERR_NEWTON_MAXIT;
+}
+
+extern "C" int ldg_set_viscosity(ldg_handle_t* h, double mu) {
+  if (!h || !(mu >= 0)) return LDG_ERR_ARG;
+  h->phys.mu = mu;
+  h->jac_age = 1 << 30;  // the retained Jacobian belongs to the old viscosity
+  return LDG_OK;
 }

@@ -20,7 +20,7 @@ FLUX = {"roe": 0, "lf": 1}
 BC = {"dirichlet": 0, "wall": 1}
 PREC_FP32, PREC_FP64 = 0, 1
 MODE_FP64, MODE_MIXED = 0, 1
-PRED_EXTRAP, PRED_GIVEN = 0, 1
+PRED_EXTRAP, PRED_GIVEN, PRED_CHECKED = 0, 1, 2
 ERRORS = {-1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_MESH", -4: "LDG_ERR_NONFINITE",
           -5: "LDG_ERR_GMRES_BREAKDOWN", -6: "LDG_ERR_NEWTON_MAXIT", -7: "LDG_ERR_NOT_BUILT",
           -8: "LDG_ERR_UNSUPPORTED", -9: "LDG_ERR_TOO_LARGE"}
@@ -57,7 +57,7 @@ class ldg_step_stats_t(C.Structure):
                 ("refine_sweeps", C.c_int32), ("res0", C.c_double), ("res_final", C.c_double),
                 ("res_pred", C.c_double), ("t_residual_ms", C.c_double),
                 ("t_jacobian_ms", C.c_double), ("t_precond_ms", C.c_double),
-                ("t_linear_ms", C.c_double)]
+                ("t_linear_ms", C.c_double), ("res_extrap", C.c_double), ("pred_weight", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +86,7 @@ _SIGS = {
     "ldg_pc_export": [_P, _P],
     "ldg_launch_count": [C.POINTER(C.c_longlong)],
     "ldg_residual_noalloc": [_P, _P, _P, _P],
+    "ldg_set_viscosity": [_P, C.c_double],
     "ldg_mlp_create": [C.c_int32, C.c_int32, C.POINTER(_P)],
     "ldg_mlp_destroy": [_P],
     "ldg_mlp_params": [_P, _P, C.c_int32],
@@ -348,7 +349,7 @@ def ldg_pc_export(P, prec):
 
 
 def solver_opts(mode=MODE_MIXED, predictor=PRED_EXTRAP, first_step=False, restart=30,
-                max_newton=50, reuse=15, max_refine=3, force_rebuild=True, rtol=1e-8,
+                max_newton=50, reuse=15, max_refine=10, force_rebuild=True, rtol=1e-8,
                 gmres_tol=1e-3):
     return ldg_solver_opts_t(mode, predictor, int(first_step), restart, max_newton, reuse,
                              max_refine, int(force_rebuild), rtol, gmres_tol)
@@ -443,3 +444,7 @@ def ldg_mlp_predict(h, m, Un, Unm1, Unm2, U0, stream=None):
     _check(lib().ldg_mlp_predict(h.ptr, m.ptr, _dptr(Un), _dptr(Unm1), _dptr(Unm2), _dptr(U0),
                                  _stream(stream)), "ldg_mlp_predict")
     return U0
+
+
+def ldg_set_viscosity(h, mu):
+    _check(lib().ldg_set_viscosity(h.ptr, float(mu)), "ldg_set_viscosity")
