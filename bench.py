@@ -61,6 +61,12 @@ def euler_residual_flops(D, p, nc, E):
     return E * (D * NL * per_line + (p + 1) ** D * nc * (D + 1))
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the timed kernels from one ncu capture of the unchanged kernel on this
+# workload; None until a capture of the current kernel exists.
+TRAFFIC = {"precond_apply": None, "jacvec": None}
+
+
 def jac_bytes(h, esz):
     """Compulsory HBM bytes of one Jacobian assembly: the K11 (+K12) values
     written plus the state read."""
@@ -120,6 +126,18 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def _nvtx(torch, name):
+    """Open (name) or close (None) the NVTX range that marks the timed FP64
+    steps, so that ncu --nvtx-include can restrict a launch list to them."""
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -152,8 +170,10 @@ def gpu_arm(args):
     dt = 0.05
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def run(mode, K, W, e2e=False):
-        """W warm-up + K timed BDF2 levels; returns per-step ms and stats."""
+    def run(mode, K, W, e2e=False, live=False):
+        """W warm-up + K timed BDF2 levels; returns per-step ms and stats.
+        With live=True the apply and matvec launches of the K timed levels
+        are bracketed by CUDA events on their stream (ldg_kernel_timer)."""
         Un = torch.from_numpy(U0).cuda()
         U1 = torch.empty_like(Un)
         ldg.ldg_newton_step(h, U1, Un, None, None, dt, ldg.solver_opts(mode=mode, first_step=True))
@@ -183,6 +203,9 @@ def gpu_arm(args):
                                         ldg.solver_opts(mode=mode, force_rebuild=True))
             e1.record(st)
             e1.synchronize()
+            if live and it == W - 1:
+                ldg.ldg_kernel_timer(True)
+                _nvtx(torch, "timed_fp64")
             if it >= W:
                 times.append(e0.elapsed_time(e1))
                 stats.append(s)
@@ -190,6 +213,8 @@ def gpu_arm(args):
                 hostbuf[0], hostbuf[1], hostbuf[2] = hostbuf[2], hostbuf[0], hostbuf[1]
             else:
                 Unm1, Un = Un, Unext
+        if live:
+            _nvtx(torch, None)
         return times, stats
 
     def kernel_ms(fn, reps=20):
@@ -214,10 +239,14 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     clk = Clocks(local)
     l0 = ldg.ldg_launch_count()
-    t64, s64 = run(ldg.MODE_FP64, args.steps, args.warmup)
+    t64, s64 = run(ldg.MODE_FP64, args.steps, args.warmup, live=True)
     launches = (ldg.ldg_launch_count() - l0)
     clocks = clk.stop()
     torch.cuda.synchronize()
+    # per-launch device time of the two Krylov kernels inside the timed steps
+    live = {name: ldg.ldg_kernel_timer_read(k, ldg.PREC_FP64)
+            for name, k in (("precond_apply", ldg.KT_APPLY), ("jacvec", ldg.KT_JACVEC))}
+    ldg.ldg_kernel_timer(False)
     ms = float(np.mean(t64))
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
@@ -271,14 +300,26 @@ def gpu_arm(args):
         "precond_apply_fp64": {"ms": t_ap64, "gbs": apply_bytes(h, 8, 8) / (t_ap64 * 1e-3) / 1e9},
         "precond_apply_fp32": {"ms": t_ap32, "gbs": apply_bytes(h, 4, 4) / (t_ap32 * 1e-3) / 1e9},
     }
-    # dominant kernel of the step by device-time share (ncu launch list,
-    # profiles/launches_euler2d_vortex_64x64_p4.md): the ILU(0) apply, bound by
-    # HBM (factors streamed once per apply); FP64 factors in the FP64 step
-    ab = apply_bytes(h, 8, 8)
-    roof = {"kernel": "k_precond_apply (FP64 factors, Euler 2-D p=4)", "bound": "hbm",
-            "achieved": ab / (t_ap64 * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": ab / (t_ap64 * 1e-3) / 1e9 / hbm, "traffic": None,
-            "bytes_per_launch": ab, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    # dominant kernel of the step: of the two Krylov kernels (the ncu launch
+    # list under profiles/ gives the shares of all kernels) the one with the
+    # larger device time inside the timed FP64 steps; both are HBM-bound
+    # streams of their matrix (factors or K11), time per launch from the
+    # live CUDA events
+    algo = {"precond_apply": apply_bytes(h, 8, 8), "jacvec": jacvec_bytes(h, 8, 8)}
+    kname = max(live, key=lambda k: live[k][1])
+    n_l, ms_l = live[kname]
+    per = ms_l / max(n_l, 1)
+    ab = algo[kname]
+    names = {"precond_apply": "k_precond_apply_staged (element ILU(0) apply, FP64)",
+             "jacvec": "k_jacvec (split matvec K11 x, FP64)"}
+    roof = {"kernel": names[kname], "bound": "hbm",
+            "achieved": ab / (per * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": ab / (per * 1e-3) / 1e9 / hbm, "traffic": TRAFFIC.get(kname),
+            "bytes_per_launch": ab, "launches_timed": n_l, "ms_per_launch": per,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, of measured)",
+            "live": {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
+                         "gbs": algo[k] / (v[1] / max(v[0], 1) * 1e-3) / 1e9,
+                         "share_of_step": v[1] / (ms * args.steps)} for k, v in live.items()}}
     kernels["residual_fp64"]["alu_frac_of_nominal_fp64"] = res_fl / (t_res * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
     out = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,

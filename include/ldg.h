@@ -366,6 +366,20 @@ int ldg_mlp_predict(ldg_handle_t* h, ldg_mlp_t* m, const double* Un, const doubl
  * counter; for benchmarks that report launches per step). */
 int ldg_launch_count(long long* out);
 
+/* Benchmark instrumentation; the paper has no counterpart. While enabled
+ * (enable != 0; each call also clears what was recorded), every launch of
+ * the preconditioner apply (kernel 0, ldg_precond_apply and inside
+ * ldg_newton_step) and of the split matvec (kernel 1) is bracketed by two
+ * CUDA events recorded on the stream it is launched on. Events are created
+ * on first use and kept for reuse. */
+int ldg_kernel_timer(int enable);
+
+/* Launches of `kernel` with vectors of precision `prec` (LDG_PREC_FP32 /
+ * LDG_PREC_FP64) recorded since the last ldg_kernel_timer call, and their
+ * summed device time in ms. Synchronizes on the recorded events.
+ * LDG_ERR_ARG for an unknown kernel or precision or null outputs. */
+int ldg_kernel_timer_read(int kernel, int prec, long long* launches, double* ms);
+
 /* Change the constant viscosity of a Navier-Stokes handle (for sweeps over
  * Reynolds numbers); a retained Jacobian is marked stale. */
 int ldg_set_viscosity(ldg_handle_t* h, double mu);

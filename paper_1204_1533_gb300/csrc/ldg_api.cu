@@ -4,10 +4,32 @@
 #include "ldg_internal.h"
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace ldg {
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
+
+// The dynamic shared-memory limit is a per-function, per-device attribute:
+// set it the first time a (kernel, device) pair needs more than the default,
+// and afterwards only when a launch asks for more than was set before.
+cudaError_t smem_attr_cached(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(fn, dev);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (err == cudaSuccess) done[key] = bytes;
+  return err;
+}
 
 cudaError_t residual_2d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
 cudaError_t residual_3d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);

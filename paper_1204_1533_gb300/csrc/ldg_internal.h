@@ -12,6 +12,14 @@ namespace ldg {
 // number of kernels this library has launched (host-side counter)
 void count_launch(int n = 1);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, calling the runtime only the first time a larger size is needed.
+cudaError_t smem_attr_cached(const void* fn, size_t bytes);
+template <typename K>
+inline cudaError_t set_smem_once(K kern, size_t bytes) {
+  return smem_attr_cached(reinterpret_cast<const void*>(kern), bytes);
+}
+
 constexpr int MAXP = 7;
 constexpr int MAXP1 = MAXP + 1;
 constexpr int MAXQ = (3 * MAXP + 2) / 2;

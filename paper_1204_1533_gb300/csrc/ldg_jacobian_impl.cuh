@@ -397,7 +397,7 @@ cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, 
   constexpr bool VISC = IsViscous<EQ>::value;
   const size_t smem = (size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0)) * sizeof(R);
   auto kern = k_jacobian<D, P, NC, EQ, R>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
   kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, K11, K12, h->geo(), h->tab, h->phys);

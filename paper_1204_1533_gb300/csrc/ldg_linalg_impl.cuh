@@ -83,12 +83,22 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
   }
 }
 
+// One thread per (line, row i): the block's lines are tile aligned and the
+// row index is the slowest thread index, so a warp reads one matrix entry of
+// 32 consecutive lines (one 128-byte segment in FP32) per load, and the
+// (p+1)-fold split gives enough loads in flight to stream K11/K12 from HBM
+// even when the mesh has few elements.
+template <int D, int P>
+struct JvShape {
+  static constexpr int THREADS = Shape<D, P>::N * Shape<D, P>::THREADS;
+};
+
 template <int D, int P, int NC, int EQ, typename R, typename V>
-__global__ void __launch_bounds__(Shape<D, P>::THREADS)
+__global__ void __launch_bounds__(JvShape<D, P>::THREADS)
     k_jacvec(const R* __restrict__ K11, const R* __restrict__ K12, const V* __restrict__ x,
              const V* __restrict__ gx, V* __restrict__ y, double shift, double scale, Geo g) {
   using S = Shape<D, P>;
-  constexpr int N = S::N, NPE = S::NPE, NCD = NC * D;
+  constexpr int N = S::N, NPE = S::NPE, NCD = NC * D, NLB = S::THREADS;
   constexpr bool VISC = IsViscous<EQ>::value;
   constexpr int tile = NC * NPE, gt = VISC ? NCD * NPE : 0;
   constexpr int64_t NK11 = (N * N + 2 * N) * NC * NC;
@@ -104,31 +114,28 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
   if constexpr (VISC)
     for (int k = threadIdx.x; k < ne * gt; k += blockDim.x) sgx[k] = gx[e0 * gt + k];
   __syncthreads();
-  const int le = threadIdx.x / S::TPE, rr = threadIdx.x % S::TPE;
+  const int i = threadIdx.x / NLB, lloc = threadIdx.x % NLB;
+  const int le = lloc / S::TPE, rr = lloc % S::TPE;
   if (le < ne) {
     const int d = rr / S::NL, l = rr % S::NL;
     const int64_t e = e0 + le;
     const int64_t L = (e * D + d) * S::NL + l;
     const int st = S::stride(d), b0 = S::base(d, l);
-    V acc[N][NC];
+    V acc[NC];
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+    for (int c = 0; c < NC; ++c) acc[c] = V(0);
+    // K11 in-line block, row i
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[i][c] = V(0);
-    // K11 in-line block
+    for (int j = 0; j < N; ++j) {
+      V xj[NC];
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+      for (int cp = 0; cp < NC; ++cp) xj[cp] = sx[le * tile + cp * NPE + b0 + j * st];
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        V xj[NC];
+      for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int cp = 0; cp < NC; ++cp) xj[cp] = sx[le * tile + cp * NPE + b0 + j * st];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int cp = 0; cp < NC; ++cp)
-            acc[i][c] += (V)K11[tile_index(L, NK11, ((i * N + j) * NC + c) * NC + cp)] * xj[cp];
-      }
+        for (int cp = 0; cp < NC; ++cp)
+          acc[c] += (V)K11[tile_index(L, NK11, ((i * N + j) * NC + c) * NC + cp)] * xj[cp];
+    }
     // K11 face blocks: outside traces of both ends
 #pragma unroll
     for (int end = 0; end < 2; ++end) {
@@ -138,26 +145,22 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
 #pragma unroll
       for (int cp = 0; cp < NC; ++cp) xo[cp] = x[(int64_t)(nb / NPE) * tile + cp * NPE + nb % NPE];
 #pragma unroll
-      for (int i = 0; i < N; ++i)
+      for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int cp = 0; cp < NC; ++cp)
-            acc[i][c] += (V)K11[tile_index(L, NK11, OFF11 + ((end * N + i) * NC + c) * NC + cp)] * xo[cp];
+        for (int cp = 0; cp < NC; ++cp)
+          acc[c] += (V)K11[tile_index(L, NK11, OFF11 + ((end * N + i) * NC + c) * NC + cp)] * xo[cp];
     }
     if constexpr (VISC) {
-#pragma unroll
-      for (int i = 0; i < N; ++i)
 #pragma unroll 1
-        for (int j = 0; j < N; ++j) {
+      for (int j = 0; j < N; ++j) {
 #pragma unroll
-          for (int cb = 0; cb < NCD; ++cb) {
-            const V gj = sgx[le * gt + cb * NPE + b0 + j * st];
+        for (int cb = 0; cb < NCD; ++cb) {
+          const V gj = sgx[le * gt + cb * NPE + b0 + j * st];
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-              acc[i][c] += (V)K12[tile_index(L, NK12, ((i * N + j) * NC + c) * NCD + cb)] * gj;
-          }
+          for (int c = 0; c < NC; ++c)
+            acc[c] += (V)K12[tile_index(L, NK12, ((i * N + j) * NC + c) * NCD + cb)] * gj;
         }
+      }
 #pragma unroll
       for (int end = 0; end < 2; ++end) {
         const int32_t nb = g.nbr[L * 2 + end];
@@ -166,18 +169,14 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
         for (int cb = 0; cb < NCD; ++cb) {
           const V go = gx[((int64_t)(nb / NPE) * NCD + cb) * NPE + nb % NPE];
 #pragma unroll
-          for (int i = 0; i < N; ++i)
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-              acc[i][c] += (V)K12[tile_index(L, NK12, OFF12 + (i * NC + c) * NCD + cb)] * go;
+          for (int c = 0; c < NC; ++c)
+            acc[c] += (V)K12[tile_index(L, NK12, OFF12 + (i * NC + c) * NCD + cb)] * go;
         }
       }
     }
     V* yo = sy + (size_t)(le * D + d) * tile;
 #pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) yo[c * NPE + b0 + i * st] = acc[i][c];
+    for (int c = 0; c < NC; ++c) yo[c * NPE + b0 + i * st] = acc[c];
   }
   __syncthreads();
   for (int k = threadIdx.x; k < ne * tile; k += blockDim.x) {
@@ -378,66 +377,203 @@ __global__ void __launch_bounds__(256)
   for (int k = tid; k < NPE * BB; k += nt) Dinv[e * NPE * BB + k] = Di[k];
 }
 
-template <int D, int P, int NC, typename R, typename V>
-__global__ void k_precond_apply(const R* __restrict__ F, const R* __restrict__ Dinv,
-                                const V* __restrict__ r, V* __restrict__ z, PcTables pt, int64_t E) {
-  using S = Shape<D, P>;
-  constexpr int N = S::N, NPE = S::NPE, W = D * P + 1, BB = NC * NC, tile = NC * NPE;
-  constexpr int NLEV = D * P + 1;
-  __shared__ V y[NPE * NC];
-  __shared__ V t[NPE * NC];
-  const int64_t e = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int i = tid / NC, c = tid % NC;
-  const bool act = tid < NPE * NC;
-  int lev = 0;
-  if (act) {
-    lev = (i % N) + ((i / N) % N) + (i / (N * N));
-    y[c * NPE + i] = r[e * tile + c * NPE + i];
-  }
-  __syncthreads();
-  const R* Fe = F + (size_t)e * NPE * W * BB;
-  // forward: y_i -= sum_{k < i} L_ik y_k, level by level
-  for (int lv = 1; lv < NLEV; ++lv) {
-    V acc = 0;
-    if (act && lev == lv) {
-      acc = y[c * NPE + i];
-      for (int s = 0; s < W; ++s) {
-        const int k = pt.pat[i * W + s];
-        if (k >= i) break;
+// ---------------------------------------------------------------------------
+// ILU(0) apply z = (L U)^-1 r. A warp holds 32 / (n_c G) elements; lane
+// (c, g) of an element owns component c of every row and the n_c / G block
+// columns m in [g n_c / G, (g + 1) n_c / G). Rows are processed in order
+// (forward 1 .. npe-1, then backward npe-1 .. 0): lane (c, g) accumulates
+// F[i][s][c][m] y[col(s)][m] over the row's pattern slots and its m range,
+// the G lanes of component c sum their parts, and lane (c, 0) stores the
+// result in the warp's y slice (shared memory). G = n_c gives the most
+// lanes per element (for FP32, where the chain is latency-bound); G = 1
+// leaves no reduction at all (for FP64, where the FP64 pipe is the limit).
+//
+// Row i = ix + N iy + N^2 iz couples to the nodes of its D lines; its
+// pattern slots in ascending column order are: lower z, lower y, lower x,
+// the diagonal (slot ix + iy + iz), upper x, upper y, upper z. The loops
+// are unrolled at compile time, so slot counts and columns are constants,
+// and the factors of the row PD steps ahead are loaded into registers while
+// the current row is reduced: the serial row chain never waits on memory.
+// (Element shapes too large to unroll run the same loop rolled, loading
+// each row's factors when it is processed.)
+template <int D, int P, int NC, int G, typename R, typename V>
+struct ApplyLanes {
+  static constexpr int N = P + 1, NPE = D == 2 ? N * N : N * N * N, W = D * P + 1, BB = NC * NC;
+  static constexpr int MPL = NC / G;            // block columns per lane
+  static constexpr int LPE = NC * G;            // lanes per element
+  static constexpr int EPW = 32 / LPE;          // elements per warp
+  static constexpr int MAXS = D * (N - 1);      // slots of one triangle in a row
+  static constexpr int TASKS = 2 * NPE - 1;     // forward rows 1.., backward rows ..0
+  static constexpr size_t YB = (size_t)EPW * NC * NPE * sizeof(V);
+  // one warp per block when a warp already holds many elements (keeps the
+  // grid a few blocks per SM on small meshes), else up to four
+  static constexpr int WPB = EPW >= 8 ? 1 : (YB * 4 <= 40960 ? 4 : (YB * 2 <= 40960 ? 2 : 1));
+  static constexpr int THREADS = 32 * WPB;
+  static constexpr int REGS_PER_ROW = MAXS * MPL * (int)(sizeof(R) / 4);
+  // the task loop is unrolled (and prefetched PD rows ahead) only while the
+  // unrolled body stays small enough for the compiler to keep fb in registers
+  static constexpr bool UNROLL = TASKS * MAXS * MPL <= 2000;
+  static constexpr int UNROLL_N = UNROLL ? TASKS : 1;
+  static constexpr int PD = !UNROLL ? 0 : (REGS_PER_ROW * 8 <= 72 ? 8 : (REGS_PER_ROW * 4 <= 72 ? 4 : 2));
+  static_assert(NC % G == 0, "G must divide n_c");
+};
+
+// sum of v over the G lanes of one component group (G consecutive lanes)
+template <int G, typename V>
+__device__ __forceinline__ V group_sum(V v, V* scratch, int lane) {
+  if constexpr (G == 1) {
+    return v;
+  } else if constexpr ((G & (G - 1)) == 0) {
 #pragma unroll
-        for (int m = 0; m < NC; ++m) acc -= (V)Fe[(i * W + s) * BB + c * NC + m] * y[m * NPE + k];
-      }
-    }
-    __syncthreads();
-    if (act && lev == lv) y[c * NPE + i] = acc;
-    __syncthreads();
-  }
-  // backward: z_i = Dinv_i (y_i - sum_{j > i} U_ij z_j), levels descending
-  for (int lv = NLEV - 1; lv >= 0; --lv) {
-    if (act && lev == lv) {
-      V acc = y[c * NPE + i];
-      for (int s = W - 1; s >= 0; --s) {
-        const int j = pt.pat[i * W + s];
-        if (j <= i) break;
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  } else {
+    scratch[lane] = v;
+    __syncwarp();
+    const int g0 = lane - lane % G;
+    V s = 0;
 #pragma unroll
-        for (int m = 0; m < NC; ++m) acc -= (V)Fe[(i * W + s) * BB + c * NC + m] * y[m * NPE + j];
-      }
-      t[c * NPE + i] = acc;
-    }
-    __syncthreads();
-    if (act && lev == lv) {
-      V v = 0;
-#pragma unroll
-      for (int m = 0; m < NC; ++m) v += (V)Dinv[((size_t)e * NPE + i) * BB + c * NC + m] * t[m * NPE + i];
-      y[c * NPE + i] = v;
-    }
-    __syncthreads();
+    for (int k = 0; k < G; ++k) s += scratch[g0 + k];
+    __syncwarp();
+    return s;
   }
-  if (act) z[e * tile + c * NPE + i] = y[c * NPE + i];
 }
 
-// ---------------------------------------------------------------------------
+// MPL consecutive factor values (vector loads where the block layout keeps
+// them aligned: the offsets are multiples of MPL elements inside 16-byte
+// aligned n_c x n_c blocks)
+template <int MPL, typename R>
+__device__ __forceinline__ void load_run(const R* p, R (&out)[MPL]) {
+  if constexpr (sizeof(R) == 8 && MPL % 2 == 0 && (MPL * 8) % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < MPL; k += 2) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(p + k));
+      out[k] = v.x;
+      out[k + 1] = v.y;
+    }
+  } else if constexpr (sizeof(R) == 4 && MPL % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < MPL; k += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p + k));
+      out[k] = v.x;
+      out[k + 1] = v.y;
+      out[k + 2] = v.z;
+      out[k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < MPL; ++k) out[k] = __ldg(p + k);
+  }
+}
+
+template <int D, int N>
+struct RowPos {
+  int i, ix, iy, iz, dg;
+  __device__ __forceinline__ constexpr RowPos(int r)
+      : i(r), ix(r % N), iy((r / N) % N), iz(D == 3 ? r / (N * N) : 0), dg(r % N + (r / N) % N + (D == 3 ? r / (N * N) : 0)) {}
+  // column of lower slot k (0 <= k < dg) and upper slot k (slot dg + 1 + k)
+  __device__ __forceinline__ constexpr int lower_col(int k) const {
+    return k < iz ? i - (iz - k) * N * N : (k < iz + iy ? i - (iy - (k - iz)) * N : i - (ix - (k - iz - iy)));
+  }
+  __device__ __forceinline__ constexpr int upper_col(int k) const {
+    return k < N - 1 - ix ? i + (k + 1)
+                          : (k < 2 * N - 2 - ix - iy ? i + (k - (N - 1 - ix) + 1) * N
+                                                     : i + (k - (2 * N - 2 - ix - iy) + 1) * N * N);
+  }
+};
+
+template <int D, int P, int NC, int G, typename R, typename V>
+__global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
+    k_precond_apply(const R* __restrict__ F, const R* __restrict__ Dinv, const V* __restrict__ r,
+                    V* __restrict__ z, int64_t E) {
+  using A = ApplyLanes<D, P, NC, G, R, V>;
+  constexpr int N = A::N, NPE = A::NPE, W = A::W, BB = A::BB, EPW = A::EPW, MPL = A::MPL;
+  constexpr int MAXS = A::MAXS, TASKS = A::TASKS, PD = A::PD, UN = A::UNROLL_N, tile = NC * NPE;
+  using Pos = RowPos<D, N>;
+  __shared__ V ys[A::WPB][EPW][tile];
+  __shared__ V tb[A::WPB][EPW][NC];
+  __shared__ V scr[A::WPB][32 + G];  // padded: idle lanes of a partial group read past lane 31
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int el = lane / A::LPE, q = lane % A::LPE, c = q / G, g = q % G, m0 = g * MPL;
+  const int64_t e = ((int64_t)blockIdx.x * A::WPB + warp) * EPW + el;
+  const bool act = el < EPW && e < E;
+  V* y = ys[warp][act ? el : 0];
+  V* tbuf = tb[warp][act ? el : 0];
+  V* sc = scr[warp];
+  if (act)
+    for (int k = q; k < tile; k += A::LPE) y[k] = r[e * tile + k];
+  const R* Fe = F + (act ? e : 0) * (int64_t)NPE * W * BB + c * NC + m0;
+  const R* De = Dinv + (act ? e : 0) * (int64_t)NPE * BB + c * NC + m0;
+  R fb[PD + 1][MAXS][MPL];
+  R db[PD + 1][MPL];
+  // factors of task t: forward row t + 1 (lower slots) or backward row
+  // 2 npe - 2 - t (upper slots and the inverted diagonal block)
+  auto fetch = [&](int t) {
+    const bool fwd = t < NPE - 1;
+    const Pos ps(fwd ? t + 1 : 2 * NPE - 2 - t);
+    const int ns = fwd ? ps.dg : MAXS - ps.dg, s0 = fwd ? 0 : ps.dg + 1, b = t % (PD + 1);
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < MAXS; ++k)
+        if (k < ns) load_run<MPL>(Fe + (ps.i * W + s0 + k) * BB, fb[b][k]);
+      if (!fwd) load_run<MPL>(De + ps.i * BB, db[b]);
+    }
+  };
+#pragma unroll
+  for (int t = 0; t < PD && t < TASKS; ++t) fetch(t);
+  __syncwarp();
+#pragma unroll UN
+  for (int t = 0; t < TASKS; ++t) {
+    if (t + PD < TASKS) fetch(t + PD);
+    const bool fwd = t < NPE - 1;
+    const Pos ps(fwd ? t + 1 : 2 * NPE - 2 - t);
+    const int b = t % (PD + 1);
+    V acc[MPL];
+#pragma unroll
+    for (int mm = 0; mm < MPL; ++mm) acc[mm] = V(0);
+    if (act) {
+      if (fwd) {
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k)
+          if (k < ps.dg) {
+            const int col = ps.lower_col(k);
+#pragma unroll
+            for (int mm = 0; mm < MPL; ++mm) acc[mm] += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k)
+          if (k < MAXS - ps.dg) {
+            const int col = ps.upper_col(k);
+#pragma unroll
+            for (int mm = 0; mm < MPL; ++mm) acc[mm] += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
+          }
+      }
+    }
+    V pv = 0;
+#pragma unroll
+    for (int mm = 0; mm < MPL; ++mm) pv += acc[mm];
+    const V s = group_sum<G>(pv, sc, lane);
+    if (fwd) {
+      if (act && g == 0) y[c * NPE + ps.i] -= s;
+      __syncwarp();
+    } else {
+      if (act && g == 0) tbuf[c] = y[c * NPE + ps.i] - s;
+      __syncwarp();
+      V d = 0;
+      if (act) {
+#pragma unroll
+        for (int mm = 0; mm < MPL; ++mm) d += (V)db[b][mm] * tbuf[m0 + mm];
+      }
+      const V zi = group_sum<G>(d, sc, lane);
+      if (act && g == 0) y[c * NPE + ps.i] = zi;
+      __syncwarp();
+    }
+  }
+  if (act)
+    for (int k = q; k < tile; k += A::LPE) z[e * tile + k] = y[k];
+}
+
 template <int D, int P, int EQ, typename R, typename V>
 cudaError_t run_jacvec(const ldg_handle* h, const R* K11, const R* K12, const R* K21, V* gbuf,
                        double shift, double scale, const V* x, V* y, cudaStream_t st) {
@@ -449,16 +585,16 @@ cudaError_t run_jacvec(const ldg_handle* h, const R* K11, const R* K12, const R*
   if constexpr (VISC) {
     const size_t sm1 = (size_t)S::EPB * (NC * S::NPE + D * NC * D * S::NPE) * sizeof(V);
     auto k1 = k_k21_apply<D, P, NC, R, V>;
-    err = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    err = set_smem_once(k1, sm1);
     if (err != cudaSuccess) return err;
     k1<<<(unsigned)blocks, S::THREADS, sm1, st>>>(K21, x, gbuf, h->geo());
     count_launch();
   }
   const size_t sm2 = (size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0) + D * NC * S::NPE) * sizeof(V);
   auto k2 = k_jacvec<D, P, NC, EQ, R, V>;
-  err = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  err = set_smem_once(k2, sm2);
   if (err != cudaSuccess) return err;
-  k2<<<(unsigned)blocks, S::THREADS, sm2, st>>>(K11, K12, x, gbuf, y, shift, scale, h->geo());
+  k2<<<(unsigned)blocks, JvShape<D, P>::THREADS, sm2, st>>>(K11, K12, x, gbuf, y, shift, scale, h->geo());
   count_launch();
   return cudaGetLastError();
 }
@@ -489,7 +625,7 @@ cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R
   const size_t smem = precond_smem<D, P, EQ, R>();
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   auto kern = k_precond<D, P, NC, VISC, R>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
   kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, F, Dinv, h->geo(), pc_tables(h), shift, scale);
   count_launch();
@@ -500,9 +636,14 @@ template <int D, int P, int EQ, typename R, typename V>
 cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const R* Dinv, const V* r, V* z,
                               cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
-  using S = Shape<D, P>;
-  const int threads = ((S::NPE * NC + 31) / 32) * 32;
-  k_precond_apply<D, P, NC, R, V><<<(unsigned)h->E, threads, 0, st>>>(F, Dinv, r, z, pc_tables(h), h->E);
+  // FP64: one lane per component (no reductions, fewest FP64 operations)
+  // while the unrolled body fits; otherwise, and for FP32, one lane per
+  // block entry (the most parallelism)
+  constexpr int G = (sizeof(V) == 8 && ApplyLanes<D, P, NC, 1, R, V>::UNROLL) ? 1 : NC;
+  using A = ApplyLanes<D, P, NC, G, R, V>;
+  const int64_t epb = (int64_t)A::EPW * A::WPB;
+  const int64_t blocks = (h->E + epb - 1) / epb;
+  k_precond_apply<D, P, NC, G, R, V><<<(unsigned)blocks, A::THREADS, 0, st>>>(F, Dinv, r, z, h->E);
   count_launch();
   return cudaGetLastError();
 }

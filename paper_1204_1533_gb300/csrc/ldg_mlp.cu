@@ -597,7 +597,7 @@ extern "C" int ldg_mlp_set_scaling(ldg_mlp_t* m, const double* in_mean, const do
 }
 
 static cudaError_t smem_attr(const void* kern) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  return ldg::smem_attr_cached(kern, sizeof(Smem));
 }
 
 extern "C" int ldg_mlp_forward(ldg_mlp_t* m, const void* X, int64_t M, float* Y, void* stream) {

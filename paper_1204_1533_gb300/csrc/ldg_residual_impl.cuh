@@ -15,6 +15,17 @@
 
 namespace ldg {
 
+// elements per block: whole 32-line tiles when a block of at most 512
+// threads can cover them (so tiled Jacobian accesses of a block never share
+// a 128-byte line with another block), otherwise about 128 threads
+__host__ __device__ constexpr int elems_per_block(int tpe) {
+  int best = 0;
+  for (int e = 1; e <= 64 && e * tpe <= 512; ++e)
+    if ((e * tpe) % 32 == 0 && (best == 0 || (e * tpe >= 64 && best * tpe < 64))) best = e;
+  if (best) return best;
+  return tpe >= 128 ? 1 : 128 / tpe;
+}
+
 template <int D, int P>
 struct Shape {
   static constexpr int N = P + 1;
@@ -22,7 +33,7 @@ struct Shape {
   static constexpr int NL = (D == 2) ? N : N * N;
   static constexpr int NQ = (3 * P + 2) / 2;
   static constexpr int TPE = D * NL;
-  static constexpr int EPB = TPE >= 128 ? 1 : 128 / TPE;
+  static constexpr int EPB = elems_per_block(TPE);
   static constexpr int THREADS = EPB * TPE;
   __device__ __forceinline__ static int stride(int d) { return d == 0 ? 1 : (d == 1 ? N : N * N); }
   __device__ __forceinline__ static int base(int d, int l) {
@@ -326,7 +337,7 @@ cudaError_t run_gradient(const ldg_handle* h, const double* U, double* Q, cudaSt
   using S = Shape<D, P>;
   const size_t smem = (size_t)S::EPB * (NC * S::NPE + D * NC * D * S::NPE) * sizeof(double);
   auto kern = k_gradient<D, P, NC>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
   kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, h->geo(), h->tab, h->phys);
@@ -343,7 +354,7 @@ cudaError_t run_residual(const ldg_handle* h, const double* U, const double* Q, 
   const size_t smem =
       (size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0) + D * NC * S::NPE) * sizeof(double);
   auto kern = k_residual<D, P, NC, EQ>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
   kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, R, h->geo(), h->tab, h->phys);
