@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (non-tensor and tensor), TFLOP/s
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per launch (documented in the design doc)
+# algorithmic work per launch
 # ---------------------------------------------------------------------------
 def euler_residual_flops(D, p, nc, E):
     """FP64 operations of one first-order residual (divisions and square
@@ -310,7 +310,7 @@ def gpu_arm(args):
     n_l, ms_l = live[kname]
     per = ms_l / max(n_l, 1)
     ab = algo[kname]
-    names = {"precond_apply": "k_precond_apply_staged (element ILU(0) apply, FP64)",
+    names = {"precond_apply": "k_precond_apply (element ILU(0) apply, FP64)",
              "jacvec": "k_jacvec (split matvec K11 x, FP64)"}
     roof = {"kernel": names[kname], "bound": "hbm",
             "achieved": ab / (per * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -346,6 +346,10 @@ def gpu_arm(args):
         "gpu_launches_per_step": launches_per_step,
         "clocks": clocks,
     }
+    if rank == 0 and ws == 1 and not args.no_tgv:
+        out["tgv"] = tgv_section(args, hbm)
+    if rank == 0 and ws == 1 and not args.no_learned:
+        out["learned"] = learned_section(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -378,6 +382,112 @@ def _oracle_step(n_sample, p):
     U1, st = S.newton_bdf2(F, jac, U0, U0, 0.05, first=False, rtol=1e-8, gmres_tol=1e-3,
                            restart=30, reuse=15, precond_builder=pc)
     return time.perf_counter() - t0, disc.ndof, st
+
+
+NS_EQ = {"kind": "ns", "gamma": 1.4, "mu": 1.0 / 1600.0, "Pr": 0.72, "flux": "roe"}
+
+
+def _kernel_ms(torch, flush, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def tgv_section(args, hbm):
+    """3-D Navier-Stokes Taylor-Green vortex, 32^3 curved hexes, p = 3
+    (10.5M DOF): the hot-path kernels at full size against the HBM roofline
+    and one BDF2 level (dt = 0.05) in mixed precision and in FP64, with the
+    relative difference of the two solutions."""
+    import torch
+
+    from paper_1204_1533_gb300 import inputs as I
+    from paper_1204_1533_gb300 import ldg
+    n, dt = args.tgv_n, args.tgv_dt
+    m = I.tgv_mesh(n, 3)
+    U0 = I.tgv_state(m)
+    t0 = time.perf_counter()
+    h = ldg.ldg_setup(m, NS_EQ)
+    t_setup = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    Ut = torch.from_numpy(U0).cuda()
+    R = torch.empty_like(Ut)
+    out = {"workload": f"ns3d_tgv_{n}^3_p3_bdf2_dt{dt}", "dof": h.ndof, "setup_s": t_setup}
+    k = {}
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_residual(h, Ut, R), 5)
+    k["residual_fp64"] = {"ms": t, "dof_s": h.ndof / (t * 1e-3)}
+    J = ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32)
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32, J), 3)
+    jb = jac_bytes(h, 4)
+    k["jacobian_fp32"] = {"ms": t, "dof_s": h.ndof / (t * 1e-3), "gbs": jb / (t * 1e-3) / 1e9,
+                          "frac_hbm": jb / (t * 1e-3) / 1e9 / hbm}
+    x = torch.randn(h.ndof, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_jacvec(h, J, 1.0, -dt, x, y, ldg.PREC_FP32), 5)
+    vb = jacvec_bytes(h, 4, 4)
+    k["jacvec_fp32"] = {"ms": t, "gbs": vb / (t * 1e-3) / 1e9, "frac_hbm": vb / (t * 1e-3) / 1e9 / hbm}
+    P = ldg.ldg_precond(h, J, 1.0, -2.0 / 3.0 * dt)
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_precond(h, J, 1.0, -2.0 / 3.0 * dt, P), 2)
+    k["precond_build_fp32"] = {"ms": t}
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_precond_apply(h, P, x, y, ldg.PREC_FP32), 5)
+    ab = apply_bytes(h, 4, 4)
+    k["precond_apply_fp32"] = {"ms": t, "gbs": ab / (t * 1e-3) / 1e9, "frac_hbm": ab / (t * 1e-3) / 1e9 / hbm}
+    out["kernels"] = k
+    del J, P, x, y
+    torch.cuda.empty_cache()
+    sol = {}
+    for name, mode in (("mixed", ldg.MODE_MIXED), ("fp64", ldg.MODE_FP64)):
+        Un = torch.from_numpy(U0).cuda()
+        U1 = torch.empty_like(Un)
+        ldg.ldg_newton_step(h, U1, Un, None, None, dt, ldg.solver_opts(mode=mode, first_step=True))
+        U2 = torch.empty_like(Un)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s = ldg.ldg_newton_step(h, U2, U1, Un, None, dt, ldg.solver_opts(mode=mode, force_rebuild=True))
+        e1.record()
+        e1.synchronize()
+        sol[name] = U2
+        out[name] = {"ms_per_step": e0.elapsed_time(e1), "newton_its": s["newton_its"], "gmres_its": s["gmres_its"],
+                     "res_final_rel": s["res_final"] / s["res0"],
+                     "phases_ms": {q: s[q] for q in ("t_residual_ms", "t_jacobian_ms", "t_precond_ms",
+                                                     "t_linear_ms")}}
+        del Un, U1
+        torch.cuda.empty_cache()
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["rel_diff_mixed_vs_fp64"] = float((sol["mixed"] - sol["fp64"]).norm() / sol["fp64"].norm())
+    del h, sol, Ut, R
+    return out
+
+
+def learned_section(args):
+    """The learned Newton guess on the Taylor-Green vortex at 16^3, p = 3:
+    trajectories from the implicit solver for Re ~ U[400, 1600], GPU
+    training, and on the held-out Re = 1200 the wall time per BDF2 level of
+    FP64 + extrapolation, mixed + extrapolation and mixed + learned guess
+    (residual-checked), all to the same 1e-8 relative residual."""
+    from paper_1204_1533_gb300 import learned
+    out, _, h = learned.experiment(n=args.learn_n, n_traj=args.learn_traj, steps=10, dt=args.learn_dt,
+                                   train_steps=args.learn_train, lines=4096, eval_steps=8, verbose=False)
+    keep = ("mesh", "p", "trajectories", "levels_per_trajectory", "dt", "samples", "train_steps", "t_generate_s",
+            "t_train_s", "loss_first", "loss_last", "held_out_re", "mean_res_ratio_mlp_over_extrap",
+            "mean_err_ratio_mlp_over_extrap", "mean_mlp_weight", "newton_extrap", "newton_mlp", "newton_fp64",
+            "gmres_extrap", "gmres_mlp", "gmres_fp64", "ms_fp64_extrap", "ms_mixed_extrap", "ms_mixed_mlp",
+            "max_rel_diff_mixed_vs_fp64")
+    res = {q: out[q] for q in keep if q in out}
+    if "ms_fp64_extrap" in res:
+        res["speedup_mixed_learned_vs_fp64"] = res["ms_fp64_extrap"] / res["ms_mixed_mlp"]
+        res["speedup_mixed_vs_fp64"] = res["ms_fp64_extrap"] / res["ms_mixed_extrap"]
+    return res
 
 
 def cpu_baseline(args):
@@ -422,6 +532,14 @@ def main():
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--cpu-sample", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tgv", action="store_true", help="skip the 3-D Taylor-Green section")
+    ap.add_argument("--tgv-n", type=int, default=32)
+    ap.add_argument("--tgv-dt", type=float, default=0.05)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess section")
+    ap.add_argument("--learn-n", type=int, default=16)
+    ap.add_argument("--learn-dt", type=float, default=0.03)
+    ap.add_argument("--learn-traj", type=int, default=24)
+    ap.add_argument("--learn-train", type=int, default=4000)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -222,6 +222,46 @@ __device__ void invert_block(const R* a, R* inv) {
     for (int c = 0; c < NC; ++c) inv[r * NC + c] = m[r][NC + c];
 }
 
+// Gauss-Jordan with partial pivoting on an NC x NC block by one warp: lane
+// t < 2 NC holds column t of the augmented matrix [a | I]; pivot columns
+// are broadcast by shuffles. Same operations per entry as invert_block.
+template <typename R, int NC>
+__device__ void invert_block_warp(const R* a, R* inv, int lane) {
+  R col[NC];
+#pragma unroll
+  for (int r = 0; r < NC; ++r)
+    col[r] = lane < NC ? a[r * NC + lane] : (lane < 2 * NC ? (r == lane - NC ? R(1) : R(0)) : R(0));
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    R pc[NC];  // column c, broadcast
+#pragma unroll
+    for (int r = 0; r < NC; ++r) pc[r] = __shfl_sync(0xffffffffu, col[r], c);
+    int piv = c;
+#pragma unroll
+    for (int r = c + 1; r < NC; ++r)
+      if (fabs((double)pc[r]) > fabs((double)pc[piv])) piv = r;
+    // swap rows c and piv (in this lane's column and in the broadcast copy)
+#pragma unroll
+    for (int r = c + 1; r < NC; ++r)
+      if (r == piv) {
+        R t = col[r];
+        col[r] = col[c];
+        col[c] = t;
+        t = pc[r];
+        pc[r] = pc[c];
+        pc[c] = t;
+      }
+    const R ip = R(1) / pc[c];
+    col[c] *= ip;
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
+      if (r != c) col[r] -= pc[r] * col[c];
+  }
+  if (lane >= NC && lane < 2 * NC)
+#pragma unroll
+    for (int r = 0; r < NC; ++r) inv[r * NC + lane - NC] = col[r];
+}
+
 struct PcTables {
   const int16_t* pat;   // [NPE][W]
   const int8_t* slot;   // [NPE][NPE]
@@ -245,9 +285,17 @@ __global__ void __launch_bounds__(256)
   R* A = reinterpret_cast<R*>(smraw);            // [NPE][W][NC][NC]
   R* Di = A + NPE * W * BB;                        // [NPE][NC][NC]
   R* K21e = Di + NPE * BB;                         // [NPE][W][D] element part of K21
+  __shared__ int16_t pat_s[NPE * W];
+  __shared__ int8_t slot_s[NPE * NPE];
+  __shared__ int16_t lvl_s[NPE];
+  __shared__ int32_t lptr_s[D * P + 2];
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   const R sc = (R)scale;
+  for (int k = tid; k < NPE * W; k += nt) pat_s[k] = pt.pat[k];
+  for (int k = tid; k < NPE * NPE; k += nt) slot_s[k] = pt.slot[k];
+  for (int k = tid; k < NPE; k += nt) lvl_s[k] = pt.lvl[k];
+  for (int k = tid; k < D * P + 2; k += nt) lptr_s[k] = pt.lptr[k];
   for (int k = tid; k < NPE * W * BB; k += nt) {
     const int i = k / (W * BB), s = (k / BB) % W, cc = k % BB;
     A[k] = (pt.pat[i * W + s] == i && cc / NC == cc % NC) ? (R)shift : R(0);
@@ -265,7 +313,7 @@ __global__ void __launch_bounds__(256)
       const int b0 = S::base(d, l);
       const int ni = b0 + i * st, nj = b0 + j * st;
       const int64_t L = (e * D + d) * NL + l;
-      const int s = pt.slot[ni * NPE + nj];
+      const int s = slot_s[ni * NPE + nj];
       A[(ni * W + s) * BB + cc] += sc * K11[tile_index(L, NK11, ((i * N + j) * NC + cc / NC) * NC + cc % NC)];
     }
     if constexpr (VISC)
@@ -274,7 +322,7 @@ __global__ void __launch_bounds__(256)
         const int b0 = S::base(d, l);
         const int ni = b0 + i * st, nj = b0 + j * st;
         const int64_t L = (e * D + d) * NL + l;
-        K21e[(ni * W + pt.slot[ni * NPE + nj]) * D + b] += K21[tile_index(L, NK21, (i * N + j) * D + b)];
+        K21e[(ni * W + slot_s[ni * NPE + nj]) * D + b] += K21[tile_index(L, NK21, (i * N + j) * D + b)];
       }
     __syncthreads();
   }
@@ -301,8 +349,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int b = 0; b < D; ++b) kb[b] = K12[tile_index(L, NK12, ((i * N + t) * NC + c) * NCD + cp * D + b)];
           for (int s2 = 0; s2 < W; ++s2) {
-            const int nj = pt.pat[ng * W + s2];
-            const int s = pt.slot[ni * NPE + nj];
+            const int nj = pat_s[ng * W + s2];
+            const int s = slot_s[ni * NPE + nj];
             if (s < 0) continue;
             R v = 0;
 #pragma unroll
@@ -331,7 +379,7 @@ __global__ void __launch_bounds__(256)
             v += K12[tile_index(L, NK12, OFF12 + (i * NC + c) * NCD + cp * D + b)] *
                  K21[tile_index(Lo, NK21, N * N * D + tpos * D + b)];
           const int nk = b0 + end * P * st;
-          accs[pt.slot[ni * NPE + nk]] += v;
+          accs[slot_s[ni * NPE + nk]] += v;
         }
       }
 #pragma unroll
@@ -339,39 +387,50 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
   }
-  // block ILU(0), IKJ order, in the pattern
+  // block ILU(0), IKJ order inside each row, in the pattern. Rows of one
+  // wavefront level (ix + iy + iz) never appear in each other's pattern, so
+  // they are factored concurrently, one warp per row; the row's updates use
+  // only rows of earlier levels.
+  {
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
 #pragma unroll 1
-  for (int i = 0; i < NPE; ++i) {
+    for (int lv = 0; lv < D * P + 1; ++lv) {
 #pragma unroll 1
-    for (int s = 0; s < W; ++s) {
-      const int k = pt.pat[i * W + s];
-      if (k >= i) break;
-      // A_ik <- A_ik Dinv_k
-      R tmp = 0;
-      if (tid < BB) {
-        const int c = tid / NC, cp = tid % NC;
+      for (int rr = lptr_s[lv] + warp; rr < lptr_s[lv + 1]; rr += nwarps) {
+        const int i = lvl_s[rr];
+#pragma unroll 1
+        for (int s = 0; s < W; ++s) {
+          const int k = pat_s[i * W + s];
+          if (k >= i) break;
+          // A_ik <- A_ik Dinv_k
+          R tmp = 0;
+          if (lane < BB) {
+            const int c = lane / NC, cp = lane % NC;
 #pragma unroll
-        for (int m = 0; m < NC; ++m) tmp += A[(i * W + s) * BB + c * NC + m] * Di[k * BB + m * NC + cp];
-      }
-      __syncthreads();
-      if (tid < BB) A[(i * W + s) * BB + tid] = tmp;
-      __syncthreads();
-      // A_ij -= A_ik A_kj for j > k in both patterns
-      for (int q = tid; q < W * BB; q += nt) {
-        const int s2 = q / BB, c = (q / NC) % NC, cp = q % NC;
-        const int j = pt.pat[i * W + s2];
-        if (j <= k) continue;
-        const int sk = pt.slot[k * NPE + j];
-        if (sk < 0) continue;
-        R v = 0;
+            for (int m = 0; m < NC; ++m) tmp += A[(i * W + s) * BB + c * NC + m] * Di[k * BB + m * NC + cp];
+          }
+          __syncwarp();
+          if (lane < BB) A[(i * W + s) * BB + lane] = tmp;
+          __syncwarp();
+          // A_ij -= A_ik A_kj for j > k in both patterns
+          for (int q = lane; q < W * BB; q += 32) {
+            const int s2 = q / BB, c = (q / NC) % NC, cp = q % NC;
+            const int j = pat_s[i * W + s2];
+            if (j <= k) continue;
+            const int sk = slot_s[k * NPE + j];
+            if (sk < 0) continue;
+            R v = 0;
 #pragma unroll
-        for (int m = 0; m < NC; ++m) v += A[(i * W + s) * BB + c * NC + m] * A[(k * W + sk) * BB + m * NC + cp];
-        A[(i * W + s2) * BB + c * NC + cp] -= v;
+            for (int m = 0; m < NC; ++m) v += A[(i * W + s) * BB + c * NC + m] * A[(k * W + sk) * BB + m * NC + cp];
+            A[(i * W + s2) * BB + c * NC + cp] -= v;
+          }
+          __syncwarp();
+        }
+        invert_block_warp<R, NC>(A + (i * W + slot_s[i * NPE + i]) * BB, Di + i * BB, lane);
+        __syncwarp();
       }
       __syncthreads();
     }
-    if (tid == 0) invert_block<R, NC>(A + (i * W + pt.slot[i * NPE + i]) * BB, Di + i * BB);
-    __syncthreads();
   }
   for (int k = tid; k < NPE * W * BB; k += nt) F[e * NPE * W * BB + k] = A[k];
   for (int k = tid; k < NPE * BB; k += nt) Dinv[e * NPE * BB + k] = Di[k];

@@ -59,14 +59,76 @@ __global__ void k_reduce_rows(const double* __restrict__ part, int nblk, double*
   }
 }
 
-// w -= sum_j h_j V_j  (h on the device)
-template <typename V>
-__global__ void k_maxpy(V* __restrict__ w, const V* __restrict__ Vb, const double* __restrict__ h, int k,
-                        int64_t n) {
+// Fused Gram-Schmidt sweeps over up to OKMAX basis vectors V_j0 .. V_j0+kk-1,
+// one pass each, w read once per element:
+//   OrthoOp::Dots       part[j][blk] = sum_i V_j[i] w[i]
+//   OrthoOp::UpdateDots w -= sum_j h_j V_j, then part[j][blk] = sum_i V_j[i] w[i]
+//   OrthoOp::UpdateNorm w -= sum_j h_j V_j, then part[0][blk] = sum_i w[i]^2
+//   OrthoOp::Update     w -= sum_j h_j V_j
+// Products and per-thread sums are in the vector precision V (FP32 for the
+// FP32 Krylov basis: its dot products are FP32 work), block partials in FP64.
+constexpr int OKMAX = 32;
+constexpr int ORTHO_BLOCKS = 304;  // partial-sum rows: two blocks of 256 threads per SM
+// FP64 sweeps over more than 16 vectors hold up to 64 doubles per thread
+// (one block per SM fits); each thread keeps KC independent loads in
+// flight, so one block per SM still streams at full bandwidth
+template <typename V, int KC>
+constexpr int ortho_blocks() { return (sizeof(V) == 8 && KC > 16) ? ORTHO_BLOCKS / 2 : ORTHO_BLOCKS; }
+enum class OrthoOp { Dots, UpdateDots, UpdateNorm, Update };
+
+// KC: vectors handled per thread, kk rounded up to a multiple of 8 (the
+// loops run to KC with j < kk guards; predicated-off FP64 operations still
+// take issue slots of the narrow FP64 pipe, so KC tracks kk)
+template <typename V, OrthoOp OP, int KC>
+__global__ void __launch_bounds__(256) k_ortho(const V* __restrict__ Vb, int64_t n, int kk, V* __restrict__ w,
+                                               const double* __restrict__ h, double* __restrict__ part) {
+  constexpr bool UPD = OP != OrthoOp::Dots;
+  constexpr bool DOTS = OP == OrthoOp::Dots || OP == OrthoOp::UpdateDots;
+  constexpr bool NORM = OP == OrthoOp::UpdateNorm;
+  __shared__ V hs[KC];
+  __shared__ double red[8][KC];
+  if (UPD && threadIdx.x < kk) hs[threadIdx.x] = (V)h[threadIdx.x];
+  __syncthreads();
+  V acc[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) acc[j] = V(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = (double)w[i];
-    for (int j = 0; j < k; ++j) s -= h[j] * (double)Vb[(int64_t)j * n + i];
-    w[i] = (V)s;
+    V v[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) v[j] = j < kk ? Vb[(int64_t)j * n + i] : V(0);
+    V s = w[i];
+    if constexpr (UPD) {
+      V p[4] = {V(0), V(0), V(0), V(0)};  // four independent chains
+#pragma unroll
+      for (int j = 0; j < KC; ++j)
+        if (j < kk) p[j & 3] += hs[j] * v[j];
+      s -= (p[0] + p[1]) + (p[2] + p[3]);
+      w[i] = s;
+    }
+    if constexpr (DOTS) {
+#pragma unroll
+      for (int j = 0; j < KC; ++j)
+        if (j < kk) acc[j] += v[j] * s;
+    }
+    if constexpr (NORM) acc[0] += s * s;
+  }
+  if constexpr (DOTS || NORM) {
+    const int nd = NORM ? 1 : kk;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      if (j < nd) {
+        double x = (double)acc[j];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wp][j] = x;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nd) {
+      double x = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x += red[k][threadIdx.x];
+      part[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = x;
+    }
   }
 }
 
@@ -133,9 +195,14 @@ struct Work {
   double* y;                                  // [m+1]
 };
 
+static size_t part_len(int m) {
+  const size_t a = (size_t)(m + 2) * MDOT_BLOCKS, b = (size_t)OKMAX * ORTHO_BLOCKS;
+  return a > b ? a : b;
+}
+
 static size_t work_bytes(const ldg_handle* h, int m, int vbytes) {
   const size_t N = (size_t)h->ndof;
-  return 6 * N * 8 + (size_t)(m + 1) * N * vbytes + 2 * N * vbytes + (size_t)(m + 2) * MDOT_BLOCKS * 8 +
+  return 6 * N * 8 + (size_t)(m + 1) * N * vbytes + 2 * N * vbytes + part_len(m) * 8 +
          3 * (size_t)(m + 2) * 8 + 64 * 256;  // plus 256-byte alignment of each piece
 }
 
@@ -164,7 +231,7 @@ static int get_work(ldg_handle* h, int m, int vbytes, Work& w) {
   w.Vb = take((size_t)(m + 1) * N * vbytes);
   w.z = take(N * vbytes);
   w.t = take(N * vbytes);
-  w.part = (double*)take((size_t)(m + 2) * MDOT_BLOCKS * 8);
+  w.part = (double*)take(part_len(m) * 8);
   w.hcol = (double*)take((size_t)(m + 2) * 8);
   w.hacc = (double*)take((size_t)(m + 2) * 8);
   w.y = (double*)take((size_t)(m + 2) * 8);
@@ -181,6 +248,63 @@ static cudaError_t mdot(const V* Vb, int k, int64_t n, const V* w, double* part,
   k_reduce_rows<<<k, 256, 0, st>>>(part, MDOT_BLOCKS, dev, accum);
   count_launch();
   return cudaGetLastError();
+}
+
+// One fused sweep (see k_ortho) over basis vectors j0 .. j0+kk-1 (kk <= OKMAX);
+// dot products or the norm land in dev[] (and are added to accum[]).
+template <typename V, OrthoOp OP>
+static cudaError_t ortho(const V* Vb, int kk, int64_t n, V* w, const double* hin, double* part, double* dev,
+                         double* accum, cudaStream_t st) {
+  int nb;
+  if (kk <= 8) {
+    nb = ortho_blocks<V, 8>();
+    k_ortho<V, OP, 8><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+  } else if (kk <= 16) {
+    nb = ortho_blocks<V, 16>();
+    k_ortho<V, OP, 16><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+  } else if (kk <= 24) {
+    nb = ortho_blocks<V, 24>();
+    k_ortho<V, OP, 24><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+  } else {
+    nb = ortho_blocks<V, OKMAX>();
+    k_ortho<V, OP, OKMAX><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+  }
+  count_launch();
+  if constexpr (OP != OrthoOp::Update) {
+    const int nd = OP == OrthoOp::UpdateNorm ? 1 : kk;
+    k_reduce_rows<<<nd, 256, 0, st>>>(part, nb, dev, accum);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+// Classical Gram-Schmidt with one re-orthogonalisation of w against
+// V_0 .. V_{k}: hacc[0..k] receives the summed coefficients, hacc[k+1] the
+// squared norm of the result. With up to OKMAX vectors this is three fused
+// sweeps (dots; update + dots; update + norm), beyond that chunked sweeps.
+template <typename V>
+static cudaError_t cgs2(const V* Vb, int kv, int64_t n, V* w, const Work& ws, cudaStream_t st) {
+  cudaError_t e;
+  if (kv <= OKMAX) {
+    if ((e = ortho<V, OrthoOp::Dots>(Vb, kv, n, w, nullptr, ws.part, ws.hcol, ws.hacc, st))) return e;
+    if ((e = ortho<V, OrthoOp::UpdateDots>(Vb, kv, n, w, ws.hcol, ws.part, ws.hcol, ws.hacc, st))) return e;
+    return ortho<V, OrthoOp::UpdateNorm>(Vb, kv, n, w, ws.hcol, ws.part, ws.hacc + kv, nullptr, st);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j0 = 0; j0 < kv; j0 += OKMAX) {
+      const int kk = kv - j0 < OKMAX ? kv - j0 : OKMAX;
+      if ((e = ortho<V, OrthoOp::Dots>(Vb + (int64_t)j0 * n, kk, n, w, nullptr, ws.part, ws.hcol + j0,
+                                       ws.hacc + j0, st)))
+        return e;
+    }
+    for (int j0 = 0; j0 < kv; j0 += OKMAX) {
+      const int kk = kv - j0 < OKMAX ? kv - j0 : OKMAX;
+      if ((e = ortho<V, OrthoOp::Update>(Vb + (int64_t)j0 * n, kk, n, w, ws.hcol + j0, ws.part, nullptr,
+                                         nullptr, st)))
+        return e;
+    }
+  }
+  return ortho<V, OrthoOp::Dots>(w, 1, n, w, nullptr, ws.part, ws.hacc + kv, nullptr, st);
 }
 
 // Right-preconditioned GMRES(m) on (I - adt A) x = b for vectors of type V;
@@ -218,12 +342,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
     if (launch_jacvec(h, h->Jn, 1.0, -adt, z, vn, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
     // classical Gram-Schmidt, twice
     LDG_CUDA_TRY(cudaMemsetAsync(w.hacc, 0, (k + 2) * sizeof(double), st));
-    for (int pass = 0; pass < 2; ++pass) {
-      if (mdot<V>(Vb, k + 1, n, vn, w.part, w.hcol, w.hacc, st) != cudaSuccess) return LDG_ERR_CUDA;
-      k_maxpy<V><<<grid_for(n), 256, 0, st>>>(vn, Vb, w.hcol, k + 1, n);
-      count_launch();
-    }
-    if (mdot<V>(vn, 1, n, vn, w.part, w.hacc + k + 1, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
+    if (cgs2<V>(Vb, k + 1, n, vn, w, st) != cudaSuccess) return LDG_ERR_CUDA;
     LDG_CUDA_TRY(cudaMemcpyAsync(hc.data(), w.hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
     LDG_CUDA_TRY(cudaStreamSynchronize(st));
     for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
@@ -361,7 +480,6 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
     rc = norm2(h, w.G, &g0, w, st);
     if (rc) return rc;
     if (mdot<double>(w.G, 1, n, w.r64, w.part, w.hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
-    count_launch(2);
     LDG_CUDA_TRY(cudaMemcpyAsync(&g01, w.hcol, sizeof(double), cudaMemcpyDeviceToHost, st));
     LDG_CUDA_TRY(cudaStreamSynchronize(st));
     const double dd = g1 * g1 - 2.0 * g01 + g0 * g0;  // ||G1 - G0||^2

@@ -116,29 +116,55 @@ def train(mlp, X, T, steps, batch=4096, lr=1e-3, seed=0, log_every=1000):
     return hist
 
 
-def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED):
-    """Solve the held-out trajectory twice per level: extrapolation vs the
-    network's checked guess; returns per-level statistics."""
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, (time.perf_counter() - t0) * 1e3
+
+
+def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
+    """Solve the held-out trajectory several times per level: extrapolation
+    vs the network's checked guess (both in `mode`) and, with with_fp64, the
+    plain FP64 solver with extrapolation; returns per-level statistics with
+    the wall time of each step (the network's prediction included)."""
     import torch
     ldg.ldg_set_viscosity(h, 1.0 / re)
     Us = [torch.from_numpy(U0).cuda()]
+    # first use of the predictor kernels (module loading) outside the timing
+    warm = torch.empty_like(Us[0])
+    ldg.ldg_mlp_predict(h, mlp, Us[0], Us[0], Us[0], warm)
+    torch.cuda.synchronize()
+    del warm
     rows = []
     for k in range(steps):
         first = k == 0
         Um1 = Us[-2] if k else None
-        ext, s_ext = _step(h, Us[-1], Um1, dt, first, mode, force=True)
+        (ext, s_ext), ms_ext = _timed(lambda: _step(h, Us[-1], Um1, dt, first, mode, force=True))
         if k >= 2:
-            guess = torch.empty_like(Us[-1])
-            ldg.ldg_mlp_predict(h, mlp, Us[-1], Us[-2], Us[-3], guess)
+            def learned_step():
+                guess = torch.empty_like(Us[-1])
+                ldg.ldg_mlp_predict(h, mlp, Us[-1], Us[-2], Us[-3], guess)
+                e_mlp = float((guess - ext).norm())
+                nn_, s_nn = _step(h, Us[-1], Um1, dt, first, mode, predictor=ldg.PRED_CHECKED, guess=guess,
+                                  force=True)
+                return nn_, s_nn, e_mlp
+            (nn_, s_nn, e_mlp), ms_nn = _timed(learned_step)
             e_ext = float((2.0 * Us[-1] - Us[-2] - ext).norm())
-            e_mlp = float((guess - ext).norm())
-            nn_, s_nn = _step(h, Us[-1], Um1, dt, first, mode, predictor=ldg.PRED_CHECKED, guess=guess, force=True)
-            rows.append({"level": k, "res0": s_ext["res0"], "res_extrap": s_ext["res_pred"],
-                         "res_mlp": s_nn["res_pred"], "mlp_weight": s_nn["pred_weight"],
-                         "err_extrap": e_ext, "err_mlp": e_mlp,
-                         "newton_extrap": s_ext["newton_its"], "newton_mlp": s_nn["newton_its"],
-                         "gmres_extrap": s_ext["gmres_its"], "gmres_mlp": s_nn["gmres_its"],
-                         "diff": float((nn_ - ext).abs().max() / ext.abs().max())})
+            row = {"level": k, "res0": s_ext["res0"], "res_extrap": s_ext["res_pred"],
+                   "res_mlp": s_nn["res_pred"], "mlp_weight": s_nn["pred_weight"],
+                   "err_extrap": e_ext, "err_mlp": e_mlp,
+                   "newton_extrap": s_ext["newton_its"], "newton_mlp": s_nn["newton_its"],
+                   "gmres_extrap": s_ext["gmres_its"], "gmres_mlp": s_nn["gmres_its"],
+                   "ms_extrap": ms_ext, "ms_mlp": ms_nn,
+                   "diff": float((nn_ - ext).abs().max() / ext.abs().max())}
+            if with_fp64:
+                (u64, s64), ms64 = _timed(lambda: _step(h, Us[-1], Um1, dt, first, ldg.MODE_FP64, force=True))
+                row.update({"ms_fp64": ms64, "newton_fp64": s64["newton_its"], "gmres_fp64": s64["gmres_its"],
+                            "diff_fp64": float((ext - u64).norm() / u64.norm())})
+            rows.append(row)
         Us.append(ext)
     return rows
 
@@ -193,7 +219,15 @@ def experiment(n=16, p=3, n_traj=200, steps=10, dt=0.03, train_steps=20000, line
            "gmres_extrap": float(np.mean([r["gmres_extrap"] for r in rows])),
            "gmres_mlp": float(np.mean([r["gmres_mlp"] for r in rows])),
            "mean_err_ratio_mlp_over_extrap": float(np.mean([r["err_mlp"] / r["err_extrap"] for r in rows])),
-           "mean_mlp_weight": float(np.mean([r["mlp_weight"] for r in rows])), "levels": rows}
+           "mean_mlp_weight": float(np.mean([r["mlp_weight"] for r in rows])),
+           "ms_mixed_extrap": float(np.mean([r["ms_extrap"] for r in rows])),
+           "ms_mixed_mlp": float(np.mean([r["ms_mlp"] for r in rows])),
+           "levels": rows}
+    if rows and "ms_fp64" in rows[0]:
+        out.update({"ms_fp64_extrap": float(np.mean([r["ms_fp64"] for r in rows])),
+                    "newton_fp64": float(np.mean([r["newton_fp64"] for r in rows])),
+                    "gmres_fp64": float(np.mean([r["gmres_fp64"] for r in rows])),
+                    "max_rel_diff_mixed_vs_fp64": float(np.max([r["diff_fp64"] for r in rows]))})
     if verbose:
         print(json.dumps({k: v for k, v in out.items() if k != "levels"}), flush=True)
     return out, mlp, h

@@ -2,7 +2,8 @@
 Jacobian-vector product, the element-block ILU(0) preconditioner and the
 Newton-BDF2 step against the oracle (complex-step Jacobians, textbook
 ILU(0) and GMRES). Tolerances: 1e-5 relative per block row for FP32 values
-(the benchmark spec), 1e-11 for the FP64 build; integer structure bit-exact."""
+(the stated FP32 Jacobian/preconditioner bound), 1e-11 for the FP64 build;
+integer structure bit-exact."""
 import math
 
 import numpy as np
