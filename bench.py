@@ -64,7 +64,7 @@ def euler_residual_flops(D, p, nc, E):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # the timed kernels from one ncu capture of the unchanged kernel on this
 # workload; None until a capture of the current kernel exists.
-TRAFFIC = {"precond_apply": None, "jacvec": None}
+TRAFFIC = {"precond_apply": None, "jacvec": None, "gram_schmidt": None}
 
 
 def jac_bytes(h, esz):
@@ -79,9 +79,11 @@ def jacvec_bytes(h, esz, vsz):
 
 
 def apply_bytes(h, esz, vsz):
-    """ILU(0) apply: factors + inverted diagonal blocks read, r read, z written."""
+    """ILU(0) apply: the Dp off-diagonal factor blocks of every row and the
+    inverted diagonal block read (the stored diagonal U blocks are not),
+    r read, z written."""
     W = h.D * h.p + 1
-    return h.E * h.npe * (W + 1) * h.nc * h.nc * esz + 2 * h.ndof * vsz
+    return h.E * h.npe * W * h.nc * h.nc * esz + 2 * h.ndof * vsz
 
 
 # ---------------------------------------------------------------------------
@@ -136,6 +138,20 @@ def _nvtx(torch, name):
             torch.cuda.nvtx.range_push(name)
     except Exception:
         pass
+
+
+def job_rate(ms_local, units_local, ws, device=None):
+    """Whole-job step time and throughput of ws replicas: each rank advances
+    units_local per step, the job's step time is the slowest rank's (max
+    over ranks), and the job advances units_local * ws per step."""
+    ms = float(ms_local)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_local * ws / (ms * 1e-3)
 
 
 def _dist():
@@ -243,25 +259,22 @@ def gpu_arm(args):
     launches = (ldg.ldg_launch_count() - l0)
     clocks = clk.stop()
     torch.cuda.synchronize()
-    # per-launch device time of the two Krylov kernels inside the timed steps
+    # device time and algorithmic work of the Krylov kernels inside the timed
+    # steps: (launches, ms, bytes, FLOPs) summed over the timed launches
     live = {name: ldg.ldg_kernel_timer_read(k, ldg.PREC_FP64)
-            for name, k in (("precond_apply", ldg.KT_APPLY), ("jacvec", ldg.KT_JACVEC))}
+            for name, k in (("precond_apply", ldg.KT_APPLY), ("jacvec", ldg.KT_JACVEC),
+                            ("gram_schmidt", ldg.KT_ORTHO))}
     ldg.ldg_kernel_timer(False)
-    ms = float(np.mean(t64))
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = job_rate(np.mean(t64), h.ndof, ws, "cuda")
     launches_per_step = launches / (args.steps + args.warmup + 1)
-    value = h.ndof * ws / (ms * 1e-3)
 
     # ---- mixed-precision steps on the same data ----------------------------
     tmx, smx = run(ldg.MODE_MIXED, args.steps, args.warmup)
-    ms_mx = float(np.mean(tmx))
+    ms_mx, value_mx = job_rate(np.mean(tmx), h.ndof, ws, "cuda")
 
     # ---- end to end through the public API with host buffers ----------------
     te2e, _ = run(ldg.MODE_FP64, max(2, args.steps // 2), 1, e2e=True)
-    ms_e2e = float(np.mean(te2e))
+    ms_e2e, value_e2e = job_rate(np.mean(te2e), h.ndof, ws, "cuda")
 
     # ---- per-kernel timings on the launching stream -------------------------
     Ut = torch.from_numpy(U0).cuda()
@@ -300,26 +313,36 @@ def gpu_arm(args):
         "precond_apply_fp64": {"ms": t_ap64, "gbs": apply_bytes(h, 8, 8) / (t_ap64 * 1e-3) / 1e9},
         "precond_apply_fp32": {"ms": t_ap32, "gbs": apply_bytes(h, 4, 4) / (t_ap32 * 1e-3) / 1e9},
     }
-    # dominant kernel of the step: of the two Krylov kernels (the ncu launch
-    # list under profiles/ gives the shares of all kernels) the one with the
-    # larger device time inside the timed FP64 steps; both are HBM-bound
-    # streams of their matrix (factors or K11), time per launch from the
-    # live CUDA events
-    algo = {"precond_apply": apply_bytes(h, 8, 8), "jacvec": jacvec_bytes(h, 8, 8)}
-    kname = max(live, key=lambda k: live[k][1])
-    n_l, ms_l = live[kname]
-    per = ms_l / max(n_l, 1)
-    ab = algo[kname]
+    # dominant kernel of the step: of the timed Krylov kernels (the ncu
+    # launch list under profiles/ gives the shares of all kernels) the one
+    # with the largest device time inside the timed FP64 steps. Achieved =
+    # its algorithmic bytes (or FP64 FLOPs) per launch over its mean launch
+    # time from the live CUDA events; the bound is the roofline it is closer to.
     names = {"precond_apply": "k_precond_apply (element ILU(0) apply, FP64)",
-             "jacvec": "k_jacvec (split matvec K11 x, FP64)"}
-    roof = {"kernel": names[kname], "bound": "hbm",
-            "achieved": ab / (per * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": ab / (per * 1e-3) / 1e9 / hbm, "traffic": TRAFFIC.get(kname),
-            "bytes_per_launch": ab, "launches_timed": n_l, "ms_per_launch": per,
-            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, of measured)",
-            "live": {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
-                         "gbs": algo[k] / (v[1] / max(v[0], 1) * 1e-3) / 1e9,
-                         "share_of_step": v[1] / (ms * args.steps)} for k, v in live.items()}}
+             "jacvec": "k_jacvec (split matvec K11 x, FP64)",
+             "gram_schmidt": "k_ortho (fused CGS2 sweeps of GMRES, FP64)"}
+    per_kernel = {}
+    for kname, (n_l, ms_l, by_l, fl_l) in live.items():
+        if n_l == 0 or ms_l <= 0:
+            continue
+        sec = ms_l * 1e-3
+        per_kernel[kname] = {"launches": n_l, "ms_per_launch": ms_l / n_l, "gbs": by_l / sec / 1e9,
+                             "tflops": fl_l / sec / 1e12, "frac_hbm": by_l / sec / 1e9 / hbm,
+                             "frac_fp64": fl_l / sec / 1e12 / FP64_PEAK_TFLOPS,
+                             "share_of_step": ms_l / (ms * args.steps),
+                             "bytes_per_launch": by_l / n_l, "flops_per_launch": fl_l / n_l}
+    kname = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches"])
+    pk = per_kernel[kname]
+    if pk["frac_fp64"] > pk["frac_hbm"]:
+        roof = {"kernel": names[kname], "bound": "alu", "achieved": pk["tflops"], "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": pk["frac_fp64"], "traffic": TRAFFIC.get(kname),
+                "flops_per_launch": pk["flops_per_launch"],
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)"}
+    else:
+        roof = {"kernel": names[kname], "bound": "hbm", "achieved": pk["gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": pk["frac_hbm"], "traffic": TRAFFIC.get(kname), "bytes_per_launch": pk["bytes_per_launch"],
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, of measured)"}
+    roof.update({"launches_timed": pk["launches"], "ms_per_launch": pk["ms_per_launch"], "live": per_kernel})
     kernels["residual_fp64"]["alu_frac_of_nominal_fp64"] = res_fl / (t_res * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
     out = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
@@ -332,7 +355,7 @@ def gpu_arm(args):
         "newton_its": float(np.mean([s["newton_its"] for s in s64])),
         "gmres_its": float(np.mean([s["gmres_its"] for s in s64])),
         "phases_ms_fp64": ph,
-        "mixed": {"ms_per_step": ms_mx, "value": h.ndof * ws / (ms_mx * 1e-3),
+        "mixed": {"ms_per_step": ms_mx, "value": value_mx,
                   "speedup_vs_fp64": ms / ms_mx,
                   "newton_its": float(np.mean([s["newton_its"] for s in smx])),
                   "gmres_its": float(np.mean([s["gmres_its"] for s in smx])),
@@ -340,7 +363,7 @@ def gpu_arm(args):
         "kernels": kernels,
         "roofline": roof,
         "hbm_peak_gbs": hbm, "hbm_peak_source": src,
-        "e2e": {"value": h.ndof * ws / (ms_e2e * 1e-3), "unit": "DOF/s",
+        "e2e": {"value": value_e2e, "unit": "DOF/s",
                 "h2d_bytes_per_step": 2 * h.ndof * 8, "d2h_bytes_per_step": h.ndof * 8},
         "gpu_launches": launches_per_step * args.steps,
         "gpu_launches_per_step": launches_per_step,
@@ -423,6 +446,7 @@ def tgv_section(args, hbm):
     R = torch.empty_like(Ut)
     out = {"workload": f"ns3d_tgv_{n}^3_p3_bdf2_dt{dt}", "dof": h.ndof, "setup_s": t_setup}
     k = {}
+    _nvtx(torch, "tgv_kernels")
     t = _kernel_ms(torch, flush, lambda: ldg.ldg_residual(h, Ut, R), 5)
     k["residual_fp64"] = {"ms": t, "dof_s": h.ndof / (t * 1e-3)}
     J = ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32)
@@ -441,6 +465,7 @@ def tgv_section(args, hbm):
     t = _kernel_ms(torch, flush, lambda: ldg.ldg_precond_apply(h, P, x, y, ldg.PREC_FP32), 5)
     ab = apply_bytes(h, 4, 4)
     k["precond_apply_fp32"] = {"ms": t, "gbs": ab / (t * 1e-3) / 1e9, "frac_hbm": ab / (t * 1e-3) / 1e9 / hbm}
+    _nvtx(torch, None)
     out["kernels"] = k
     del J, P, x, y
     torch.cuda.empty_cache()
@@ -452,10 +477,12 @@ def tgv_section(args, hbm):
         U2 = torch.empty_like(Un)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _nvtx(torch, f"tgv_step_{name}")
         e0.record()
         s = ldg.ldg_newton_step(h, U2, U1, Un, None, dt, ldg.solver_opts(mode=mode, force_rebuild=True))
         e1.record()
         e1.synchronize()
+        _nvtx(torch, None)
         sol[name] = U2
         out[name] = {"ms_per_step": e0.elapsed_time(e1), "newton_its": s["newton_its"], "gmres_its": s["gmres_its"],
                      "res_final_rel": s["res_final"] / s["res0"],

@@ -368,17 +368,27 @@ int ldg_launch_count(long long* out);
 
 /* Benchmark instrumentation; the paper has no counterpart. While enabled
  * (enable != 0; each call also clears what was recorded), every launch of
- * the preconditioner apply (kernel 0, ldg_precond_apply and inside
- * ldg_newton_step) and of the split matvec (kernel 1) is bracketed by two
- * CUDA events recorded on the stream it is launched on. Events are created
- * on first use and kept for reuse. */
+ * the timed kernels is bracketed by two CUDA events recorded on the stream
+ * it is launched on, and carries its algorithmic work. Timed kernels:
+ *   LDG_KT_APPLY  (0) the ILU(0) apply (ldg_precond_apply, inside
+ *                     ldg_newton_step): bytes = factors read
+ *                     E (p+1)^D (Dp+1) n_c^2 + r read + z written;
+ *   LDG_KT_JACVEC (1) the split matvec: bytes = K11 + K12 values + x + y;
+ *   LDG_KT_ORTHO  (2) each GMRES Gram-Schmidt sweep: bytes = basis vectors
+ *                     read + w read (+ written), FLOPs = 2 per multiply-add.
+ * Events are created on first use and kept for reuse. */
+#define LDG_KT_APPLY 0
+#define LDG_KT_JACVEC 1
+#define LDG_KT_ORTHO 2
 int ldg_kernel_timer(int enable);
 
 /* Launches of `kernel` with vectors of precision `prec` (LDG_PREC_FP32 /
- * LDG_PREC_FP64) recorded since the last ldg_kernel_timer call, and their
- * summed device time in ms. Synchronizes on the recorded events.
- * LDG_ERR_ARG for an unknown kernel or precision or null outputs. */
-int ldg_kernel_timer_read(int kernel, int prec, long long* launches, double* ms);
+ * LDG_PREC_FP64) recorded since the last ldg_kernel_timer call, their summed
+ * device time in ms and summed algorithmic bytes and FLOPs (either pointer
+ * may be null). Synchronizes on the recorded events. LDG_ERR_ARG for an
+ * unknown kernel or precision or null launches/ms. */
+int ldg_kernel_timer_read(int kernel, int prec, long long* launches, double* ms, double* bytes,
+                          double* flops);
 
 /* Change the constant viscosity of a Navier-Stokes handle (for sweeps over
  * Reynolds numbers); a retained Jacobian is marked stale. */

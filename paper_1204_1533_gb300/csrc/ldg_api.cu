@@ -7,10 +7,45 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 namespace ldg {
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
+
+namespace {
+struct KernelTimer {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;  // reusable events, two per recorded launch
+  struct Rec {
+    int kind;  // kernel * 2 + (vector precision FP64)
+    double bytes, flops;
+  };
+  std::vector<Rec> recs;
+};
+KernelTimer g_kt;
+}  // namespace
+
+int timer_begin(int kernel, int vprec, cudaStream_t st, double bytes, double flops) {
+  std::lock_guard<std::mutex> lock(g_kt.mu);
+  if (!g_kt.on) return -1;
+  const size_t need = 2 * (g_kt.recs.size() + 1);
+  while (g_kt.pool.size() < need) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+    g_kt.pool.push_back(ev);
+  }
+  const int slot = (int)g_kt.recs.size();
+  g_kt.recs.push_back({kernel * 2 + (vprec == LDG_PREC_FP32 ? 0 : 1), bytes, flops});
+  cudaEventRecord(g_kt.pool[2 * slot], st);
+  return slot;
+}
+
+void timer_end(int slot, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_kt.mu);
+  if (slot >= 0 && 2 * (size_t)slot + 1 < g_kt.pool.size()) cudaEventRecord(g_kt.pool[2 * slot + 1], st);
+}
 
 // The dynamic shared-memory limit is a per-function, per-device attribute:
 // set it the first time a (kernel, device) pair needs more than the default,
@@ -126,5 +161,39 @@ extern "C" int ldg_norm2(ldg_handle_t* h, const double* x, int64_t n, double* ou
 extern "C" int ldg_launch_count(long long* out) {
   if (!out) return LDG_ERR_ARG;
   *out = ldg::g_launches.load();
+  return LDG_OK;
+}
+
+extern "C" int ldg_kernel_timer(int enable) {
+  std::lock_guard<std::mutex> lock(ldg::g_kt.mu);
+  ldg::g_kt.on = enable != 0;
+  ldg::g_kt.recs.clear();
+  return LDG_OK;
+}
+
+extern "C" int ldg_kernel_timer_read(int kernel, int prec, long long* launches, double* ms, double* bytes,
+                                     double* flops) {
+  if (kernel < 0 || kernel >= ldg::KT_COUNT || (prec != LDG_PREC_FP32 && prec != LDG_PREC_FP64) || !launches ||
+      !ms)
+    return LDG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(ldg::g_kt.mu);
+  const int want = kernel * 2 + (prec == LDG_PREC_FP32 ? 0 : 1);
+  long long n = 0;
+  double tot = 0.0, by = 0.0, fl = 0.0;
+  for (size_t k = 0; k < ldg::g_kt.recs.size(); ++k) {
+    if (ldg::g_kt.recs[k].kind != want) continue;
+    cudaEvent_t a = ldg::g_kt.pool[2 * k], b = ldg::g_kt.pool[2 * k + 1];
+    if (cudaEventSynchronize(b) != cudaSuccess) return LDG_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) return LDG_ERR_CUDA;
+    tot += t;
+    by += ldg::g_kt.recs[k].bytes;
+    fl += ldg::g_kt.recs[k].flops;
+    ++n;
+  }
+  *launches = n;
+  *ms = tot;
+  if (bytes) *bytes = by;
+  if (flops) *flops = fl;
   return LDG_OK;
 }

@@ -12,6 +12,22 @@ namespace ldg {
 // number of kernels this library has launched (host-side counter)
 void count_launch(int n = 1);
 
+// Event timing of selected kernels (ldg_kernel_timer): while enabled, each
+// timed launch is bracketed by two events on its stream and carries its
+// algorithmic bytes and FLOPs.
+enum { KT_APPLY = 0, KT_JACVEC = 1, KT_ORTHO = 2, KT_COUNT = 3 };
+int timer_begin(int kernel, int vprec, cudaStream_t st, double bytes, double flops);  // slot or -1
+void timer_end(int slot, cudaStream_t st);
+struct TimedScope {
+  int slot;
+  cudaStream_t st;
+  TimedScope(int k, int vprec, cudaStream_t s, double bytes, double flops)
+      : slot(timer_begin(k, vprec, s, bytes, flops)), st(s) {}
+  ~TimedScope() {
+    if (slot >= 0) timer_end(slot, st);
+  }
+};
+
 // Raise a kernel's dynamic shared-memory limit to `bytes` on the current
 // device, calling the runtime only the first time a larger size is needed.
 cudaError_t smem_attr_cached(const void* fn, size_t bytes);

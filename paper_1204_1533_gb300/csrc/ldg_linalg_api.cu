@@ -1,6 +1,5 @@
 // C-ABI entry points of the Jacobian, split matvec and preconditioner.
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "ldg_ops.h"
@@ -39,44 +38,11 @@ cudaError_t launch_k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st) {
   LDG_DISPATCH(h, k21(h, J, st));
   return cudaErrorInvalidValue;
 }
-// Optional event timing of the two Krylov kernels: while enabled every
-// launch of kernel k (0 apply, 1 matvec) at vector precision v is bracketed
-// by two events on its own stream; the pairs are read back on demand.
-namespace {
-struct KernelTimer {
-  std::mutex mu;
-  bool on = false;
-  std::vector<cudaEvent_t> pool;          // reusable events
-  size_t used = 0;
-  std::vector<int> slot;                  // per recorded pair: k * 2 + v
-};
-KernelTimer g_kt;
-
-struct TimedLaunch {
-  int idx = -1;
-  cudaStream_t st;
-  TimedLaunch(int k, int vprec, cudaStream_t s) : st(s) {
-    std::lock_guard<std::mutex> lock(g_kt.mu);
-    if (!g_kt.on) return;
-    while (g_kt.pool.size() < g_kt.used + 2) {
-      cudaEvent_t ev;
-      if (cudaEventCreate(&ev) != cudaSuccess) return;
-      g_kt.pool.push_back(ev);
-    }
-    idx = (int)g_kt.used;
-    g_kt.used += 2;
-    g_kt.slot.push_back(k * 2 + (vprec == LDG_PREC_FP32 ? 0 : 1));
-    cudaEventRecord(g_kt.pool[idx], st);
-  }
-  ~TimedLaunch() {
-    if (idx >= 0) cudaEventRecord(g_kt.pool[idx + 1], st);
-  }
-};
-}  // namespace
-
 cudaError_t launch_jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                           const void* x, void* y, int vprec, cudaStream_t st) {
-  TimedLaunch tl(1, vprec, st);
+  const double esz = J->prec == LDG_PREC_FP32 ? 4.0 : 8.0, vsz = vprec == LDG_PREC_FP32 ? 4.0 : 8.0;
+  TimedScope tl(KT_JACVEC, vprec, st,
+                (double)h->ntiles() * 32.0 * (h->nk11() + h->nk12()) * esz + 2.0 * h->ndof * vsz, 0.0);
   LDG_DISPATCH(h, jacvec(h, J, shift, scale, x, y, vprec, st));
   return cudaErrorInvalidValue;
 }
@@ -91,7 +57,9 @@ cudaError_t launch_precond(const ldg_handle* h, const ldg_jac* J, double shift, 
 }
 cudaError_t launch_precond_apply(const ldg_handle* h, const ldg_pc* P, const void* r, void* z,
                                  int vprec, cudaStream_t st) {
-  TimedLaunch tl(0, vprec, st);
+  const double esz = P->prec == LDG_PREC_FP32 ? 4.0 : 8.0, vsz = vprec == LDG_PREC_FP32 ? 4.0 : 8.0;
+  TimedScope tl(KT_APPLY, vprec, st,
+                (double)h->E * h->npe * h->pat_w() * h->nc * h->nc * esz + 2.0 * h->ndof * vsz, 0.0);
   LDG_DISPATCH(h, apply(h, P, r, z, vprec, st));
   return cudaErrorInvalidValue;
 }
@@ -226,33 +194,4 @@ extern "C" int ldg_pc_export(const ldg_pc_t* P, void* factors) {
   const ldg_handle* h = P->h;
   const size_t bytes = (size_t)h->E * h->npe * h->pat_w() * h->nc * h->nc * esize(P->prec);
   return cudaMemcpy(factors, P->F, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
-}
-
-extern "C" int ldg_kernel_timer(int enable) {
-  std::lock_guard<std::mutex> lock(g_kt.mu);
-  g_kt.on = enable != 0;
-  g_kt.used = 0;
-  g_kt.slot.clear();
-  return LDG_OK;
-}
-
-extern "C" int ldg_kernel_timer_read(int kernel, int prec, long long* launches, double* ms) {
-  if (kernel < 0 || kernel > 1 || (prec != LDG_PREC_FP32 && prec != LDG_PREC_FP64) || !launches || !ms)
-    return LDG_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_kt.mu);
-  const int want = kernel * 2 + (prec == LDG_PREC_FP32 ? 0 : 1);
-  long long n = 0;
-  double tot = 0.0;
-  for (size_t k = 0; k < g_kt.slot.size(); ++k) {
-    if (g_kt.slot[k] != want) continue;
-    cudaEvent_t a = g_kt.pool[2 * k], b = g_kt.pool[2 * k + 1];
-    if (cudaEventSynchronize(b) != cudaSuccess) return LDG_ERR_CUDA;
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) return LDG_ERR_CUDA;
-    tot += t;
-    ++n;
-  }
-  *launches = n;
-  *ms = tot;
-  return LDG_OK;
 }

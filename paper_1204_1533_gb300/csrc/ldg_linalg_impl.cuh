@@ -464,9 +464,9 @@ struct ApplyLanes {
   static constexpr int MAXS = D * (N - 1);      // slots of one triangle in a row
   static constexpr int TASKS = 2 * NPE - 1;     // forward rows 1.., backward rows ..0
   static constexpr size_t YB = (size_t)EPW * NC * NPE * sizeof(V);
-  // one warp per block when a warp already holds many elements (keeps the
-  // grid a few blocks per SM on small meshes), else up to four
-  static constexpr int WPB = EPW >= 8 ? 1 : (YB * 4 <= 40960 ? 4 : (YB * 2 <= 40960 ? 2 : 1));
+  // small blocks spread a small mesh evenly over the SMs: one warp per block
+  // when a warp holds several elements, else two
+  static constexpr int WPB = EPW >= 4 ? 1 : (YB * 2 <= 40960 ? 2 : 1);
   static constexpr int THREADS = 32 * WPB;
   static constexpr int REGS_PER_ROW = MAXS * MPL * (int)(sizeof(R) / 4);
   // the task loop is unrolled (and prefetched PD rows ahead) only while the
@@ -691,20 +691,36 @@ cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R
   return cudaGetLastError();
 }
 
-template <int D, int P, int EQ, typename R, typename V>
-cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const R* Dinv, const V* r, V* z,
-                              cudaStream_t st) {
-  constexpr int NC = NComp<EQ, D>::value;
-  // FP64: one lane per component (no reductions, fewest FP64 operations)
-  // while the unrolled body fits; otherwise, and for FP32, one lane per
-  // block entry (the most parallelism)
-  constexpr int G = (sizeof(V) == 8 && ApplyLanes<D, P, NC, 1, R, V>::UNROLL) ? 1 : NC;
+template <int D, int P, int NC, int G, typename R, typename V>
+cudaError_t launch_apply_lanes(const ldg_handle* h, const R* F, const R* Dinv, const V* r, V* z, cudaStream_t st) {
   using A = ApplyLanes<D, P, NC, G, R, V>;
   const int64_t epb = (int64_t)A::EPW * A::WPB;
   const int64_t blocks = (h->E + epb - 1) / epb;
   k_precond_apply<D, P, NC, G, R, V><<<(unsigned)blocks, A::THREADS, 0, st>>>(F, Dinv, r, z, h->E);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int D, int P, int EQ, typename R, typename V>
+cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const R* Dinv, const V* r, V* z,
+                              cudaStream_t st) {
+  constexpr int NC = NComp<EQ, D>::value;
+  // FP32: one lane per block entry (the most parallelism). FP64: one lane
+  // per component (no reductions, fewest FP64 operations) when the mesh
+  // gives at least six such warps per SM, else two lanes per component
+  // (twice the warps for a few more FP64 additions); shapes too large to
+  // unroll use one lane per entry.
+  if constexpr (sizeof(V) == 8 && ApplyLanes<D, P, NC, 1, R, V>::UNROLL) {
+    if constexpr (NC % 2 == 0) {
+      const int64_t warps_g1 = (h->E + ApplyLanes<D, P, NC, 1, R, V>::EPW - 1) / ApplyLanes<D, P, NC, 1, R, V>::EPW;
+      int dev = 0, sms = 152;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (warps_g1 < 6 * (int64_t)sms) return launch_apply_lanes<D, P, NC, 2, R, V>(h, F, Dinv, r, z, st);
+    }
+    return launch_apply_lanes<D, P, NC, 1, R, V>(h, F, Dinv, r, z, st);
+  } else {
+    return launch_apply_lanes<D, P, NC, NC, R, V>(h, F, Dinv, r, z, st);
+  }
 }
 
 }  // namespace ldg

@@ -115,13 +115,34 @@ __global__ void __launch_bounds__(256) k_ortho(const V* __restrict__ Vb, int64_t
   if constexpr (DOTS || NORM) {
     const int nd = NORM ? 1 : kk;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if constexpr (NORM) {
+      double x = (double)acc[0];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[wp][0] = x;
+    } else {
+      // warp sums of KC values by recursive halving: each exchange step
+      // halves the values a lane holds, so a lane ends with the warp total
+      // of value (lane mod KP) after KP - 1 + log2(32 / KP) additions (a
+      // butterfly per value would take 5 KC); every FP64 addition of a warp
+      // costs the narrow FP64 pipe
+      constexpr int KP = KC <= 8 ? 8 : (KC <= 16 ? 16 : 32);
+      double v[KP];
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-      if (j < nd) {
-        double x = (double)acc[j];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[wp][j] = x;
+      for (int j = 0; j < KP; ++j) v[j] = j < KC ? (double)acc[j] : 0.0;
+#pragma unroll
+      for (int half = KP / 2; half >= 1; half >>= 1) {
+        const bool up = (lane & half) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+          const double keep = up ? v[half + k] : v[k];
+          const double send = up ? v[k] : v[half + k];
+          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
       }
+      double x = v[0];
+#pragma unroll
+      for (int o = KP; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane < KP && lane < nd) red[wp][lane] = x;
     }
     __syncthreads();
     if (threadIdx.x < nd) {
@@ -255,19 +276,26 @@ static cudaError_t mdot(const V* Vb, int k, int64_t n, const V* w, double* part,
 template <typename V, OrthoOp OP>
 static cudaError_t ortho(const V* Vb, int kk, int64_t n, V* w, const double* hin, double* part, double* dev,
                          double* accum, cudaStream_t st) {
+  constexpr bool UPD = OP != OrthoOp::Dots;
+  const double vsz = sizeof(V), nn = (double)n;
+  const double fma_per = OP == OrthoOp::UpdateDots ? 2.0 * kk : (OP == OrthoOp::UpdateNorm ? kk + 1.0 : kk);
   int nb;
-  if (kk <= 8) {
-    nb = ortho_blocks<V, 8>();
-    k_ortho<V, OP, 8><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-  } else if (kk <= 16) {
-    nb = ortho_blocks<V, 16>();
-    k_ortho<V, OP, 16><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-  } else if (kk <= 24) {
-    nb = ortho_blocks<V, 24>();
-    k_ortho<V, OP, 24><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-  } else {
-    nb = ortho_blocks<V, OKMAX>();
-    k_ortho<V, OP, OKMAX><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+  {  // the timed region is the sweep; the row reduction follows
+    TimedScope tl(KT_ORTHO, sizeof(V) == 4 ? LDG_PREC_FP32 : LDG_PREC_FP64, st,
+                  nn * vsz * (kk + 1 + (UPD ? 1 : 0)), 2.0 * nn * fma_per);
+    if (kk <= 8) {
+      nb = ortho_blocks<V, 8>();
+      k_ortho<V, OP, 8><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+    } else if (kk <= 16) {
+      nb = ortho_blocks<V, 16>();
+      k_ortho<V, OP, 16><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+    } else if (kk <= 24) {
+      nb = ortho_blocks<V, 24>();
+      k_ortho<V, OP, 24><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+    } else {
+      nb = ortho_blocks<V, OKMAX>();
+      k_ortho<V, OP, OKMAX><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
+    }
   }
   count_launch();
   if constexpr (OP != OrthoOp::Update) {

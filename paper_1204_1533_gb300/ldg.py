@@ -86,7 +86,8 @@ _SIGS = {
     "ldg_pc_export": [_P, _P],
     "ldg_launch_count": [C.POINTER(C.c_longlong)],
     "ldg_kernel_timer": [C.c_int32],
-    "ldg_kernel_timer_read": [C.c_int32, C.c_int32, C.POINTER(C.c_longlong), C.POINTER(C.c_double)],
+    "ldg_kernel_timer_read": [C.c_int32, C.c_int32, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "ldg_residual_noalloc": [_P, _P, _P, _P],
     "ldg_set_viscosity": [_P, C.c_double],
     "ldg_mlp_create": [C.c_int32, C.c_int32, C.POINTER(_P)],
@@ -371,7 +372,7 @@ def ldg_launch_count():
     return v.value
 
 
-KT_APPLY, KT_JACVEC = 0, 1
+KT_APPLY, KT_JACVEC, KT_ORTHO = 0, 1, 2
 
 
 def ldg_kernel_timer(enable=True):
@@ -379,10 +380,12 @@ def ldg_kernel_timer(enable=True):
 
 
 def ldg_kernel_timer_read(kernel, prec):
-    """(launches, summed device ms) of one timed kernel at one vector precision."""
-    n, ms = C.c_longlong(), C.c_double()
-    _check(lib().ldg_kernel_timer_read(kernel, prec, C.byref(n), C.byref(ms)), "ldg_kernel_timer_read")
-    return n.value, ms.value
+    """(launches, summed device ms, summed bytes, summed FLOPs) of one timed
+    kernel at one vector precision."""
+    n, ms, by, fl = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib().ldg_kernel_timer_read(kernel, prec, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)),
+           "ldg_kernel_timer_read")
+    return n.value, ms.value, by.value, fl.value
 
 
 def ldg_residual_noalloc(h, U, R, stream=None):
