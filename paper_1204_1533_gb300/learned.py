@@ -133,9 +133,11 @@ def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
     import torch
     ldg.ldg_set_viscosity(h, 1.0 / re)
     Us = [torch.from_numpy(U0).cuda()]
-    # first use of the predictor kernels (module loading) outside the timing
+    # first use of the predictor kernels and of the torch ops used below
+    # (module loading) outside the timing
     warm = torch.empty_like(Us[0])
     ldg.ldg_mlp_predict(h, mlp, Us[0], Us[0], Us[0], warm)
+    float((warm - Us[0]).norm())
     torch.cuda.synchronize()
     del warm
     rows = []
@@ -144,14 +146,15 @@ def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
         Um1 = Us[-2] if k else None
         (ext, s_ext), ms_ext = _timed(lambda: _step(h, Us[-1], Um1, dt, first, mode, force=True))
         if k >= 2:
+            pred = torch.empty_like(Us[-1])
+
             def learned_step():
                 guess = torch.empty_like(Us[-1])
                 ldg.ldg_mlp_predict(h, mlp, Us[-1], Us[-2], Us[-3], guess)
-                e_mlp = float((guess - ext).norm())
-                nn_, s_nn = _step(h, Us[-1], Um1, dt, first, mode, predictor=ldg.PRED_CHECKED, guess=guess,
-                                  force=True)
-                return nn_, s_nn, e_mlp
-            (nn_, s_nn, e_mlp), ms_nn = _timed(learned_step)
+                pred.copy_(guess)  # the guess before the solver overwrites it
+                return _step(h, Us[-1], Um1, dt, first, mode, predictor=ldg.PRED_CHECKED, guess=guess, force=True)
+            (nn_, s_nn), ms_nn = _timed(learned_step)
+            e_mlp = float((pred - ext).norm())
             e_ext = float((2.0 * Us[-1] - Us[-2] - ext).norm())
             row = {"level": k, "res0": s_ext["res0"], "res_extrap": s_ext["res_pred"],
                    "res_mlp": s_nn["res_pred"], "mlp_weight": s_nn["pred_weight"],

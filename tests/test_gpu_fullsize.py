@@ -1,0 +1,107 @@
+"""Parity at the workloads' full sizes, on sampled elements.
+
+The 64x64, p=4 Euler vortex and the 32^3, p=3 Navier-Stokes Taylor-Green
+vortex run through the C ABI exactly as bench.py runs them (residual,
+Jacobian, split matvec, preconditioner build and apply, FP32 and FP64). The
+oracle cannot assemble these sizes, but every checked quantity of an element
+depends only on the elements within two face steps (the residual through
+the neighbours' gradients, the matvec through K21 of the neighbours, the
+ILU(0) solve only on the element's own block), so the oracle evaluates it
+exactly on a sub-mesh cut around a sampled interior element:
+  - the residual and the matvec on the 5^D elements around it; the matvec
+    reference is the directional derivative of the full residual,
+    A x = d/de R(U + e x, D(U + e x)), by one complex step;
+  - the element's diagonal block of A on the 3^D elements around it, by a
+    complex step per column, then the oracle's masking, ILU(0) and solve.
+Tolerances as in the small cases: residual 1e-12 relative to the field's
+max-norm (taken from the float64 oracle over the whole mesh), or twice the
+float64 oracle's own distance from the extended-precision reference where
+float64 cannot resolve that; matvec 1e-5 (FP32) / 1e-11 (FP64) and apply
+1e-4 (FP32) / 1e-10 (FP64) relative to the element's max-norm."""
+import types
+
+import numpy as np
+import pytest
+
+from paper_1204_1533_gb300 import inputs as I
+from oracle import solvers as S
+from oracle.residual import Discretization, full_residual
+from submesh import H_CS, diag_block, oracle_eq, submesh
+
+pytestmark = pytest.mark.gpu
+
+SHIFT, SCALE = 1.0, -0.05
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1204_1533_gb300 import build, ldg
+    build.build()
+    return ldg
+
+
+def _workload(name):
+    if name == "vortex64_p4":
+        m = I.vortex_mesh(64, 4)
+        return m, {"kind": "euler", "gamma": 1.4, "flux": "roe"}, I.smooth_perturbation(m, I.vortex_state(m), 0.05)
+    m = I.tgv_mesh(32, 3)
+    eq = {"kind": "ns", "gamma": 1.4, "flux": "roe", "mu": 1.0 / 1600.0, "Pr": 0.72}
+    return m, eq, I.smooth_perturbation(m, I.tgv_state(m), 0.05)
+
+
+@pytest.mark.parametrize("name", ["vortex64_p4", "tgv32_p3"])
+def test_full_size_sampled_parity(L, name):
+    import torch
+    m, eq, U = _workload(name)
+    h = L.ldg_setup(m, eq)
+    Ut = torch.from_numpy(U).cuda()
+    R = torch.empty_like(Ut)
+    L.ldg_residual(h, Ut, R)
+    Rg = R.cpu().numpy()
+    x = np.random.default_rng(17).standard_normal(U.shape)
+    ys, zs = {}, {}
+    for prec in (L.PREC_FP32, L.PREC_FP64):
+        dt = torch.float32 if prec == L.PREC_FP32 else torch.float64
+        xt = torch.from_numpy(x).to(dt).cuda()
+        J = L.ldg_jacobian(h, Ut, prec)
+        y = torch.empty_like(xt)
+        L.ldg_jacvec(h, J, SHIFT, SCALE, xt, y, prec)
+        P = L.ldg_precond(h, J, SHIFT, SCALE)
+        z = torch.empty_like(xt)
+        L.ldg_precond_apply(h, P, xt, z, prec)
+        torch.cuda.synchronize()
+        ys[prec], zs[prec] = y.double().cpu().numpy(), z.double().cpu().numpy()
+        del J, P, xt, y, z
+        torch.cuda.empty_cache()
+    # the field's max-norm: the float64 oracle over the whole mesh
+    Rmax = np.abs(full_residual(Discretization(m, eq), U)).max()
+    D, n = m["D"], m["shape"]
+    pat = S.line_pattern(D, m["p"])
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        center = tuple(int(rng.integers(2, n[d] - 2)) for d in range(D))
+        sub5, ids5, k5 = submesh(m, center, 2)
+        e = ids5[k5]
+        disc5 = Discretization(sub5, oracle_eq(eq))
+        U5 = U[ids5]
+        # residual of the element
+        Ro = full_residual(disc5, np.asarray(U5, np.longdouble), np.asarray(U5, np.longdouble)).astype(np.float64)
+        floor64 = np.abs(full_residual(disc5, U5, U5)[k5] - Ro[k5]).max()
+        err = np.abs(Rg[e] - Ro[k5]).max()
+        assert err <= max(1e-12 * Rmax, 2.0 * floor64), (name, center, err, floor64, Rmax)
+        # split matvec: y = shift x + scale A x, A x by one complex step
+        Ax = np.imag(full_residual(disc5, U5 + 1j * H_CS * x[ids5], U5))[k5] / H_CS
+        y_ref = SHIFT * x[e] + SCALE * Ax
+        ny = np.abs(y_ref).max()
+        assert np.abs(ys[L.PREC_FP32][e] - y_ref).max() <= 1e-5 * ny, (name, center, "jacvec fp32")
+        assert np.abs(ys[L.PREC_FP64][e] - y_ref).max() <= 1e-11 * ny, (name, center, "jacvec fp64")
+        # ILU(0) of the element's masked block and its solve
+        sub3, ids3, k3 = submesh(m, center, 1)
+        disc3 = Discretization(sub3, oracle_eq(eq))
+        blk = diag_block(disc3, U[ids3], k3)
+        one = types.SimpleNamespace(E=1, nc=U.shape[1], npe=U.shape[2], D=D, p=m["p"])
+        F = S.ilu0(S.masked_blocks(one, blk, SHIFT, SCALE), pat)
+        z_ref = S.ilu_apply(F, pat, x[e][None])[0]
+        nz = np.abs(z_ref).max()
+        assert np.abs(zs[L.PREC_FP32][e] - z_ref).max() <= 1e-4 * nz, (name, center, "apply fp32")
+        assert np.abs(zs[L.PREC_FP64][e] - z_ref).max() <= 1e-10 * nz, (name, center, "apply fp64")
