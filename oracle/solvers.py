@@ -15,7 +15,11 @@
   * Newton's method on the BDF2 stage equation
     G(U) = U - 4/3 U^n + 1/3 U^{n-1} - 2/3 dt F(U) (BDF1 on the first step),
     solving (I - 2/3 dt A) delta = -G(U) (the form of Eq. 39 with the stage
-    residual on the right-hand side), stopping at ||G|| <= rtol ||G(U^n)||.
+    residual on the right-hand side), stopping at ||G|| <= rtol ||G(U^n)||;
+  * the paper's own integrator, Alexander's three-stage L-stable DIRK (Sec.
+    4.1, Eqs. dirk1-dirk2 and their tableau): every stage equation
+    U_i - alpha dt F(U_i) = U^n + dt sum_{j<i} a_ij K_j is the BDF1 form
+    above with U^n replaced by its right-hand side and dt by alpha dt.
 """
 from __future__ import annotations
 
@@ -200,3 +204,41 @@ def newton_bdf2(F, jac, Un, Unm1, dt, first=False, rtol=1e-8, gmres_tol=1e-3,
         age += 1
         U = U + dx.reshape(U.shape)
     raise RuntimeError("Newton did not converge")
+
+
+# ---------------------------------------------------------------------------
+# DIRK3 (Sec. 4.1)
+# ---------------------------------------------------------------------------
+DIRK3_ALPHA = 0.435866521508459
+
+
+def dirk3_tableau():
+    """(A, b, c) of the three-stage method: diagonal alpha; tau2 = (1 +
+    alpha) / 2; b1 = -(6 alpha^2 - 16 alpha + 1) / 4; b2 = (6 alpha^2 - 20
+    alpha + 5) / 4; last row of A equal to b (stiffly accurate)."""
+    a = DIRK3_ALPHA
+    tau2 = (1.0 + a) / 2.0
+    b1 = -(6.0 * a * a - 16.0 * a + 1.0) / 4.0
+    b2 = (6.0 * a * a - 20.0 * a + 5.0) / 4.0
+    A = np.array([[a, 0.0, 0.0], [tau2 - a, a, 0.0], [b1, b2, a]])
+    b = np.array([b1, b2, a])
+    c = np.array([a, tau2, 1.0])
+    return A, b, c
+
+
+def dirk3_step(F, jac, Un, dt, rtol=1e-8, gmres_tol=1e-3, restart=30, reuse=15, maxit=50,
+               precond_builder=None):
+    """One DIRK3 step: stages K_i = F(U_i) with U_i = U^n + dt sum_{j<=i}
+    a_ij K_j, each solved by Newton on G_i(U) = U - B_i - a_ii dt F(U),
+    B_i = U^n + dt sum_{j<i} a_ij K_j, from the start U = B_i; then
+    U^{n+1} = U^n + dt sum_j b_j K_j. Returns (U^{n+1}, per-stage stats)."""
+    A, b, _ = dirk3_tableau()
+    K, stats = [], []
+    for i in range(3):
+        B = Un + dt * sum(A[i, j] * K[j] for j in range(i)) if i else Un.copy()
+        Ui, st = newton_bdf2(F, jac, B, None, A[i, i] * dt, first=True, rtol=rtol, gmres_tol=gmres_tol,
+                             restart=restart, reuse=reuse, maxit=maxit, precond_builder=precond_builder)
+        K.append(F(Ui))
+        stats.append(st)
+    return Un + dt * sum(b[j] * K[j] for j in range(3)), stats
+

@@ -167,3 +167,49 @@ def test_preconditioner_reduces_gmres_iterations():
                          tol=1e-8, restart=300)
     _, it_n, _ = S.gmres(mv, b, None, tol=1e-8, restart=300)
     assert it_n > 2 * it_p
+
+
+def test_dirk3_tableau_order_conditions_and_stability():
+    """Alexander's three-stage DIRK (Sec. 4.1): the order-3 conditions, the
+    defining cubic of its diagonal, stiff accuracy and L-stability."""
+    A, b, c = S.dirk3_tableau()
+    a = S.DIRK3_ALPHA
+    assert abs(a ** 3 - 3 * a ** 2 + 1.5 * a - 1.0 / 6.0) < 1e-14
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15)
+    assert abs(b.sum() - 1.0) < 1e-15
+    assert abs(b @ c - 0.5) < 1e-14
+    assert abs(b @ c ** 2 - 1.0 / 3.0) < 1e-14
+    assert abs(b @ A @ c - 1.0 / 6.0) < 1e-14
+    assert np.array_equal(A[2], b)                     # stiffly accurate
+
+    def R(z):                                          # stability function
+        return 1.0 + z * b @ np.linalg.solve(np.eye(3) - z * A, np.ones(3))
+    assert abs(R(-1e8)) < 1e-7                         # L-stable
+    for y in np.linspace(0.0, 50.0, 101):
+        assert abs(R(1j * y)) <= 1.0 + 1e-12           # A-stable on the imaginary axis
+    # R(z) = e^z + O(z^4)
+    for z in (1e-2, -1e-2):
+        assert abs(R(z) - math.exp(z)) < 2 * abs(z) ** 4
+
+
+def test_dirk3_third_order_on_dg_advection():
+    """The DIRK3 driver on the DG advection semi-discretisation (a linear
+    ODE system): halving dt divides the error by about 8."""
+    m = I.structured_mesh((3, 3), 3, (0, 0), (1, 1), (True, True), perturb=0.1)
+    disc = Discretization(m, {"kind": "advection", "adv": [1.0, 0.6]})
+    x, y = m["nodes"][..., 0], m["nodes"][..., 1]
+    U0 = np.sin(2 * math.pi * x + 0.3)[:, None] * np.cos(2 * math.pi * y)[:, None]
+    F = lambda X: full_residual(disc, X)
+    K = JAC.K11(disc, U0)
+    jac = lambda X: (K, None, None)
+
+    def run(nsteps, T=0.2):
+        U = U0.copy()
+        for _ in range(nsteps):
+            U, st = S.dirk3_step(F, jac, U, T / nsteps, rtol=1e-13, gmres_tol=1e-14, restart=200, reuse=100)
+            assert all(s["newton"] <= 2 for s in st)
+        return U
+    ref = run(64)
+    e1 = np.abs(run(4) - ref).max()
+    e2 = np.abs(run(8) - ref).max()
+    assert 2.7 < math.log2(e1 / e2) < 3.5, (e1, e2)
