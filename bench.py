@@ -276,6 +276,30 @@ def gpu_arm(args):
     te2e, _ = run(ldg.MODE_FP64, max(2, args.steps // 2), 1, e2e=True)
     ms_e2e, value_e2e = job_rate(np.mean(te2e), h.ndof, ws, "cuda")
 
+    # ---- the paper's own integrator: DIRK3 on the same workload -------------
+    dirk = {}
+    for name, opts in (("fp64", ldg.solver_opts(mode=ldg.MODE_FP64, force_rebuild=False)),
+                       ("mixed", ldg.solver_opts(mode=ldg.MODE_MIXED, force_rebuild=False)),
+                       ("fp64_paper_policy", ldg.paper_policy_opts(mode=ldg.MODE_FP64))):
+        U = torch.from_numpy(U0).cuda()
+        Un = U
+        U = torch.empty_like(Un)
+        ldg.ldg_dirk3_step(h, U, Un, dt, opts)           # warm-up step (builds the Jacobian)
+        tt, ss = [], []
+        for _ in range(2):
+            Un, U = U, torch.empty_like(U)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s = ldg.ldg_dirk3_step(h, U, Un, dt, opts)
+            e1.record(st)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1))
+            ss.append(s)
+        dirk[name] = {"ms_per_step": float(np.mean(tt)), "newton_its": float(np.mean([s["newton_its"] for s in ss])),
+                      "gmres_its": float(np.mean([s["gmres_its"] for s in ss])),
+                      "jac_builds": float(np.mean([s["jac_builds"] for s in ss]))}
+
     # ---- per-kernel timings on the launching stream -------------------------
     Ut = torch.from_numpy(U0).cuda()
     R = torch.empty_like(Ut)
@@ -361,6 +385,8 @@ def gpu_arm(args):
                   "gmres_its": float(np.mean([s["gmres_its"] for s in smx])),
                   "phases_ms": {k: float(np.mean([s[k] for s in smx])) for k in ph}},
         "kernels": kernels,
+        "dirk3": dict(dirk, note="one step of the paper's three-stage DIRK on the same workload and dt, "
+                                 "Jacobian re-used across stages and steps (the paper's policy)"),
         "roofline": roof,
         "hbm_peak_gbs": hbm, "hbm_peak_source": src,
         "e2e": {"value": value_e2e, "unit": "DOF/s",

@@ -275,6 +275,8 @@ typedef struct {
   int32_t force_rebuild; /* 1: build K, P at the first Newton iteration       */
   double rtol;           /* ||G(U)||_2 <= rtol ||G(U^n)||_2                  */
   double gmres_tol;      /* relative tolerance of each linear solve           */
+  int32_t stall_rebuild; /* 1: also rebuild K, P when a Newton step fails to
+                            halve ||G|| (an addition to the paper's policy)   */
 } ldg_solver_opts_t;
 
 typedef struct {
@@ -306,6 +308,25 @@ typedef struct {
 int ldg_newton_step(ldg_handle_t* h, double* U_next, const double* U_n, const double* U_nm1,
                     const double* U_nm2, double dt, const ldg_solver_opts_t* opts,
                     ldg_step_stats_t* stats, void* stream);
+
+/*
+ * One step of the paper's own integrator, Alexander's L-stable three-stage
+ * third-order DIRK (Sec. 4.1, Eqs. dirk1-dirk2 and their tableau, diagonal
+ * alpha = 0.435866521508459): stage i solves
+ *   U_i - alpha dt R(U_i) = B_i,   B_i = U^n + dt sum_{j<i} a_ij K_j,
+ * by the Newton-GMRES solver of ldg_newton_step (its BDF1 form with U^n
+ * replaced by B_i and dt by alpha dt, started from B_i), K_i = R(U_i), and
+ * U^{n+1} = U^n + dt sum_j b_j K_j. All stages share (I - alpha dt A), so
+ * the Jacobian and preconditioner are re-used across stages and steps under
+ * opts->reuse (the paper's policy); opts->force_rebuild applies to the first
+ * stage only, opts->first_step and opts->predictor are ignored. U_next and
+ * U_n: device FP64 [ndof], distinct. stats: counts and phase times summed
+ * over the three stages; res0 / res_final / res_pred of the last stage.
+ * Work buffers (5 ndof doubles) are allocated on first use and kept with
+ * the handle. Synchronises on stream. Errors as ldg_newton_step.
+ */
+int ldg_dirk3_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt,
+                   const ldg_solver_opts_t* opts, ldg_step_stats_t* stats, void* stream);
 
 /* ---- learned Newton predictor (not in the paper) ------------------------
  * A line-local MLP n_in -> 128 -> 128 -> 128 -> n_out with GELU (tanh form)

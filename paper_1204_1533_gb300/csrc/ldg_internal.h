@@ -116,6 +116,7 @@ struct ldg_handle {
   void* ws = nullptr;        // solver workspace
   size_t ws_bytes = 0;
   double* Qbuf = nullptr;    // LDG gradient of the last residual [E][nc][D][npe]
+  double* dirk = nullptr;    // DIRK3 stage vectors K1..K3, B, U_i [5][ndof]
   double* red = nullptr;     // reduction scratch (doubles)
   int64_t red_len = 0;
   ldg::Geo geo() const {

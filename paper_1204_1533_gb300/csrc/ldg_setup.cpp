@@ -627,6 +627,7 @@ extern "C" int ldg_destroy(ldg_handle_t* h) {
   cudaFree(h->gD);
   cudaFree(h->src);
   cudaFree(h->Qbuf);
+  cudaFree(h->dirk);
   cudaFree(h->red);
   cudaFree(h->nbf);
   cudaFree(h->linemet);

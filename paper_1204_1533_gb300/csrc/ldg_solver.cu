@@ -543,7 +543,7 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
     stats->res_final = gn;
     if (gn <= target) return LDG_OK;
     if (it == o->max_newton) break;
-    if (it > 0 && gn > 0.5 * gprev) rebuild = true;  // slow convergence: refresh the Jacobian
+    if (o->stall_rebuild && it > 0 && gn > 0.5 * gprev) rebuild = true;  // slow convergence: refresh the Jacobian
     gprev = gn;
     if (rebuild || h->jac_age > o->reuse) {
       {
@@ -622,6 +622,68 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
     h->jac_age++;
   }
   return LDG_ERR_NEWTON_MAXIT;
+}
+
+// dst = base + c0 K0 + c1 K1 + c2 K2 (terms with null K skipped)
+__global__ void k_lincomb3(double* __restrict__ dst, const double* __restrict__ base, const double* __restrict__ K0,
+                           const double* __restrict__ K1, const double* __restrict__ K2, double c0, double c1,
+                           double c2, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = base[i];
+    if (K0) v += c0 * K0[i];
+    if (K1) v += c1 * K1[i];
+    if (K2) v += c2 * K2[i];
+    dst[i] = v;
+  }
+}
+
+// Alexander's three-stage DIRK (Sec. 4.1): every stage is the BDF1 Newton
+// problem of ldg_newton_step with U^n -> B_i and dt -> alpha dt.
+extern "C" int ldg_dirk3_step(ldg_handle_t* h, double* U, const double* Un, double dt,
+                              const ldg_solver_opts_t* o, ldg_step_stats_t* stats, void* stream) {
+  if (!h || !U || !Un || !o || !stats || !(dt > 0) || U == Un) return LDG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->ndof;
+  if (!h->dirk) LDG_CUDA_TRY(cudaMalloc((void**)&h->dirk, 5 * (size_t)n * sizeof(double)));
+  double* K[3] = {h->dirk, h->dirk + n, h->dirk + 2 * n};
+  double* B = h->dirk + 3 * n;
+  double* Ui = h->dirk + 4 * n;
+  const double al = 0.435866521508459;
+  const double tau2 = (1.0 + al) / 2.0;
+  const double b1 = -(6.0 * al * al - 16.0 * al + 1.0) / 4.0, b2 = (6.0 * al * al - 20.0 * al + 5.0) / 4.0;
+  const double A[3][3] = {{al, 0.0, 0.0}, {tau2 - al, al, 0.0}, {b1, b2, al}};
+  const double b[3] = {b1, b2, al};
+  *stats = ldg_step_stats_t{};
+  for (int i = 0; i < 3; ++i) {
+    k_lincomb3<<<grid_for(n), 256, 0, st>>>(B, Un, i > 0 ? K[0] : nullptr, i > 1 ? K[1] : nullptr, nullptr,
+                                            dt * A[i][0], dt * A[i][1], 0.0, n);
+    count_launch();
+    ldg_solver_opts_t oi = *o;
+    oi.first_step = 1;
+    oi.predictor = LDG_PRED_EXTRAP;  // BDF1 start: U = B_i
+    if (i > 0) oi.force_rebuild = 0;
+    ldg_step_stats_t si;
+    int rc = ldg_newton_step(h, Ui, B, nullptr, nullptr, al * dt, &oi, &si, stream);
+    if (rc) return rc;
+    stats->newton_its += si.newton_its;
+    stats->gmres_its += si.gmres_its;
+    stats->jac_builds += si.jac_builds;
+    stats->refine_sweeps += si.refine_sweeps;
+    stats->t_residual_ms += si.t_residual_ms;
+    stats->t_jacobian_ms += si.t_jacobian_ms;
+    stats->t_precond_ms += si.t_precond_ms;
+    stats->t_linear_ms += si.t_linear_ms;
+    stats->res0 = si.res0;
+    stats->res_final = si.res_final;
+    stats->res_pred = si.res_pred;
+    rc = ldg_residual(h, Ui, K[i], stream);
+    if (rc) return rc;
+  }
+  k_lincomb3<<<grid_for(n), 256, 0, st>>>(U, Un, K[0], K[1], K[2], dt * b[0], dt * b[1], dt * b[2], n);
+  count_launch();
+  LDG_CUDA_TRY(cudaGetLastError());
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  return LDG_OK;
 }
 
 extern "C" int ldg_set_viscosity(ldg_handle_t* h, double mu) {

@@ -49,7 +49,7 @@ class ldg_solver_opts_t(C.Structure):
     _fields_ = [("mode", C.c_int32), ("predictor", C.c_int32), ("first_step", C.c_int32),
                 ("restart", C.c_int32), ("max_newton", C.c_int32), ("reuse", C.c_int32),
                 ("max_refine", C.c_int32), ("force_rebuild", C.c_int32),
-                ("rtol", C.c_double), ("gmres_tol", C.c_double)]
+                ("rtol", C.c_double), ("gmres_tol", C.c_double), ("stall_rebuild", C.c_int32)]
 
 
 class ldg_step_stats_t(C.Structure):
@@ -102,6 +102,7 @@ _SIGS = {
     "ldg_mlp_predict": [_P, _P, _P, _P, _P, _P, _P],
     "ldg_newton_step": [_P, _P, _P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t),
                         C.POINTER(ldg_step_stats_t), _P],
+    "ldg_dirk3_step": [_P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t), C.POINTER(ldg_step_stats_t), _P],
 }
 
 
@@ -353,9 +354,9 @@ def ldg_pc_export(P, prec):
 
 def solver_opts(mode=MODE_MIXED, predictor=PRED_EXTRAP, first_step=False, restart=30,
                 max_newton=50, reuse=15, max_refine=10, force_rebuild=True, rtol=1e-8,
-                gmres_tol=1e-3):
+                gmres_tol=1e-3, stall_rebuild=True):
     return ldg_solver_opts_t(mode, predictor, int(first_step), restart, max_newton, reuse,
-                             max_refine, int(force_rebuild), rtol, gmres_tol)
+                             max_refine, int(force_rebuild), rtol, gmres_tol, int(stall_rebuild))
 
 
 def ldg_newton_step(h, U_next, U_n, U_nm1, U_nm2, dt, opts, stream=None):
@@ -364,6 +365,21 @@ def ldg_newton_step(h, U_next, U_n, U_nm1, U_nm2, dt, opts, stream=None):
                                  float(dt), C.byref(opts), C.byref(st), _stream(stream)),
            "ldg_newton_step")
     return st.as_dict()
+
+
+def ldg_dirk3_step(h, U_next, U_n, dt, opts, stream=None):
+    st = ldg_step_stats_t()
+    _check(lib().ldg_dirk3_step(h.ptr, _dptr(U_next), _dptr(U_n), float(dt), C.byref(opts), C.byref(st),
+                                _stream(stream)), "ldg_dirk3_step")
+    return st.as_dict()
+
+
+def paper_policy_opts(mode=MODE_FP64, rtol=1e-8, max_newton=50):
+    """The paper's Newton policy for DIRK3 (Sec. 5.5): a fixed five GMRES
+    iterations per Newton step, Jacobian and preconditioner re-used until the
+    Newton iterations since the last rebuild exceed 15."""
+    return solver_opts(mode=mode, restart=5, max_refine=1, gmres_tol=0.0, reuse=15, force_rebuild=False,
+                       rtol=rtol, max_newton=max_newton, stall_rebuild=False)
 
 
 def ldg_launch_count():

@@ -284,3 +284,55 @@ def test_newton_bdf2_step(L, mode, name):
     d1 = np.abs(U1.cpu().numpy() - U1o).max() / np.abs(U1o).max()
     d2 = np.abs(U2.cpu().numpy() - U2o).max() / np.abs(U2o).max()
     assert d1 < 1e-7 and d2 < 1e-7, (d1, d2)
+
+
+def _oracle_newton_parts(disc):
+    F = lambda X: full_residual(disc, X)
+
+    def jac(X):
+        if disc.eq["kind"] == "ns":
+            Qx = gradient(disc, X)
+            return JAC.K11(disc, X, Qx), JAC.K12(disc, X, Qx), JAC.K21(disc)
+        return JAC.K11(disc, X), None, None
+    return F, jac
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", ["euler2d_p3", "ns2d_p2"])
+def test_dirk3_step(L, mode, name):
+    """One step of the paper's three-stage DIRK (Sec. 4.1) against the
+    oracle's DIRK3 with every stage solved to 1e-12."""
+    import torch
+    m, eq, U0, _ = _case(name)
+    disc = Discretization(m, _oeq(eq))
+    dt = 0.05 if name.startswith("euler") else 0.01
+    F, jac = _oracle_newton_parts(disc)
+    Uo, _ = S.dirk3_step(F, jac, U0, dt, rtol=1e-12, gmres_tol=1e-10, restart=400, reuse=1)
+    h = L.ldg_setup(m, eq)
+    Un = torch.from_numpy(U0).cuda()
+    U1 = torch.empty_like(Un)
+    st = L.ldg_dirk3_step(h, U1, Un, dt, L.solver_opts(mode=mode))
+    assert st["res_final"] <= 1e-8 * st["res0"]
+    assert st["newton_its"] <= 30
+    d = np.abs(U1.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    assert d < 1e-7, d
+
+
+def test_dirk3_paper_policy(L):
+    """The paper's Newton policy (five GMRES iterations per Newton step,
+    Jacobian re-use until more than 15 Newton iterations) reaches the same
+    levels as the default solver over two DIRK3 steps."""
+    import torch
+    m, eq, U0, _ = _case("euler2d_p3")
+    h = L.ldg_setup(m, eq)
+    out = {}
+    for name, opts in (("default", L.solver_opts(mode=0)), ("paper", L.paper_policy_opts(mode=0))):
+        U = torch.from_numpy(U0).cuda()
+        for _ in range(2):
+            Un, U = U, torch.empty_like(U)
+            st = L.ldg_dirk3_step(h, U, Un, 0.05, opts)
+            assert st["res_final"] <= 1e-8 * st["res0"], (name, st)
+            if name == "paper":
+                assert st["gmres_its"] == 5 * st["newton_its"]
+        out[name] = U.cpu().numpy()
+    assert np.abs(out["paper"] - out["default"]).max() <= 1e-7 * np.abs(out["default"]).max()
