@@ -19,7 +19,9 @@
   * the paper's own integrator, Alexander's three-stage L-stable DIRK (Sec.
     4.1, Eqs. dirk1-dirk2 and their tableau): every stage equation
     U_i - alpha dt F(U_i) = U^n + dt sum_{j<i} a_ij K_j is the BDF1 form
-    above with U^n replaced by its right-hand side and dt by alpha dt.
+    above with U^n replaced by its right-hand side and dt by alpha dt;
+  * the classical explicit fourth-order Runge-Kutta step the paper uses for
+    explicit time-stepping (Sec. 4.1).
 """
 from __future__ import annotations
 
@@ -241,4 +243,14 @@ def dirk3_step(F, jac, Un, dt, rtol=1e-8, gmres_tol=1e-3, restart=30, reuse=15, 
         K.append(F(Ui))
         stats.append(st)
     return Un + dt * sum(b[j] * K[j] for j in range(3)), stats
+
+
+def rk4_step(F, U, dt):
+    """Classical RK4: k1 = F(U), k2 = F(U + dt/2 k1), k3 = F(U + dt/2 k2),
+    k4 = F(U + dt k3); U + dt/6 (k1 + 2 k2 + 2 k3 + k4)."""
+    k1 = F(U)
+    k2 = F(U + 0.5 * dt * k1)
+    k3 = F(U + 0.5 * dt * k2)
+    k4 = F(U + dt * k3)
+    return U + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
 

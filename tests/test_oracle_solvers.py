@@ -213,3 +213,32 @@ def test_dirk3_third_order_on_dg_advection():
     e1 = np.abs(run(4) - ref).max()
     e2 = np.abs(run(8) - ref).max()
     assert 2.7 < math.log2(e1 / e2) < 3.5, (e1, e2)
+
+
+def test_rk4_amplification_is_the_quartic_taylor_polynomial():
+    """On y' = M y one step multiplies by 1 + hM + (hM)^2/2 + (hM)^3/6 + (hM)^4/24."""
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((6, 6))
+    y = rng.standard_normal(6)
+    h = 0.1
+    hm = h * M
+    P = np.eye(6) + hm + hm @ hm / 2 + hm @ hm @ hm / 6 + hm @ hm @ hm @ hm / 24
+    assert np.allclose(S.rk4_step(lambda v: M @ v, y, h), P @ y, rtol=1e-14, atol=1e-14)
+
+
+def test_rk4_fourth_order_on_dg_advection():
+    m = I.structured_mesh((3, 3), 3, (0, 0), (1, 1), (True, True), perturb=0.1)
+    disc = Discretization(m, {"kind": "advection", "adv": [1.0, 0.6]})
+    x, y = m["nodes"][..., 0], m["nodes"][..., 1]
+    U0 = np.sin(2 * math.pi * x + 0.3)[:, None] * np.cos(2 * math.pi * y)[:, None]
+    F = lambda X: full_residual(disc, X)
+
+    def run(nsteps, T=0.1):
+        U = U0.copy()
+        for _ in range(nsteps):
+            U = S.rk4_step(F, U, T / nsteps)
+        return U
+    ref = run(256)
+    e1 = np.abs(run(32) - ref).max()
+    e2 = np.abs(run(64) - ref).max()
+    assert 3.7 < math.log2(e1 / e2) < 4.4, (e1, e2)
