@@ -328,6 +328,19 @@ int ldg_newton_step(ldg_handle_t* h, double* U_next, const double* U_n, const do
 int ldg_dirk3_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt,
                    const ldg_solver_opts_t* opts, ldg_step_stats_t* stats, void* stream);
 
+/*
+ * One step of the classical explicit fourth-order Runge-Kutta method, the
+ * paper's explicit time-stepping of dU/dt = R(U, D(U)) (Sec. 4.1):
+ * K1 = R(U^n), K2 = R(U^n + dt/2 K1), K3 = R(U^n + dt/2 K2),
+ * K4 = R(U^n + dt K3), U_next = U^n + dt/6 (K1 + 2 K2 + 2 K3 + K4).
+ * U_next and U_n: device FP64 [ndof] (may be the same array). Four
+ * residual evaluations, enqueued on stream without synchronising; work
+ * buffers (5 ndof doubles, shared with ldg_dirk3_step) are allocated on
+ * first use and kept with the handle. No stability check: dt is the
+ * caller's.
+ */
+int ldg_rk4_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt, void* stream);
+
 /* ---- learned Newton predictor (not in the paper) ------------------------
  * A line-local MLP n_in -> 128 -> 128 -> 128 -> n_out with GELU (tanh form)
  * predicts, for every line of reference direction 1, the correction to the

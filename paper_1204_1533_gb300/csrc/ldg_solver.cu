@@ -624,8 +624,8 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
   return LDG_ERR_NEWTON_MAXIT;
 }
 
-// dst = base + c0 K0 + c1 K1 + c2 K2 (terms with null K skipped)
-__global__ void k_lincomb3(double* __restrict__ dst, const double* __restrict__ base, const double* __restrict__ K0,
+// dst = base + c0 K0 + c1 K1 + c2 K2 (terms with null K skipped; dst may be base)
+__global__ void k_lincomb3(double* dst, const double* base, const double* __restrict__ K0,
                            const double* __restrict__ K1, const double* __restrict__ K2, double c0, double c1,
                            double c2, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -683,6 +683,30 @@ extern "C" int ldg_dirk3_step(ldg_handle_t* h, double* U, const double* Un, doub
   count_launch();
   LDG_CUDA_TRY(cudaGetLastError());
   LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  return LDG_OK;
+}
+
+// Classical RK4 (Sec. 4.1, explicit time-stepping).
+extern "C" int ldg_rk4_step(ldg_handle_t* h, double* U, const double* Un, double dt, void* stream) {
+  if (!h || !U || !Un || !(dt > 0)) return LDG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->ndof;
+  if (!h->dirk) LDG_CUDA_TRY(cudaMalloc((void**)&h->dirk, 5 * (size_t)n * sizeof(double)));
+  double* K[4] = {h->dirk, h->dirk + n, h->dirk + 2 * n, h->dirk + 3 * n};
+  double* Y = h->dirk + 4 * n;
+  const double c[3] = {0.5 * dt, 0.5 * dt, dt};
+  int rc = ldg_residual(h, Un, K[0], stream);
+  if (rc) return rc;
+  for (int s = 0; s < 3; ++s) {
+    k_lincomb3<<<grid_for(n), 256, 0, st>>>(Y, Un, K[s], nullptr, nullptr, c[s], 0.0, 0.0, n);
+    count_launch();
+    rc = ldg_residual(h, Y, K[s + 1], stream);
+    if (rc) return rc;
+  }
+  k_lincomb3<<<grid_for(n), 256, 0, st>>>(U, Un, K[0], K[1], K[2], dt / 6.0, dt / 3.0, dt / 3.0, n);
+  k_lincomb3<<<grid_for(n), 256, 0, st>>>(U, U, K[3], nullptr, nullptr, dt / 6.0, 0.0, 0.0, n);
+  count_launch(2);
+  LDG_CUDA_TRY(cudaGetLastError());
   return LDG_OK;
 }
 

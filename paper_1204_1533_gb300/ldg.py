@@ -103,6 +103,7 @@ _SIGS = {
     "ldg_newton_step": [_P, _P, _P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t),
                         C.POINTER(ldg_step_stats_t), _P],
     "ldg_dirk3_step": [_P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t), C.POINTER(ldg_step_stats_t), _P],
+    "ldg_rk4_step": [_P, _P, _P, C.c_double, _P],
 }
 
 
@@ -372,6 +373,10 @@ def ldg_dirk3_step(h, U_next, U_n, dt, opts, stream=None):
     _check(lib().ldg_dirk3_step(h.ptr, _dptr(U_next), _dptr(U_n), float(dt), C.byref(opts), C.byref(st),
                                 _stream(stream)), "ldg_dirk3_step")
     return st.as_dict()
+
+
+def ldg_rk4_step(h, U_next, U_n, dt, stream=None):
+    _check(lib().ldg_rk4_step(h.ptr, _dptr(U_next), _dptr(U_n), float(dt), _stream(stream)), "ldg_rk4_step")
 
 
 def paper_policy_opts(mode=MODE_FP64, rtol=1e-8, max_newton=50):
