@@ -203,6 +203,13 @@ int ldg_residual_uq(ldg_handle_t* h, const double* U, const double* Q, double* R
  *   K21         : scalar, in-line [(i (p+1) + j) D + b][L], face
  *                 [KOFF + i D + b][L] for the end whose u^ comes from outside
  * (entry-major, line-minor: a thread per line reads coalesced).
+ * On meshes with no-slip walls (LDG_BC_WALL; Euler and Navier-Stokes) K11
+ * and K12 include the wall flux, and the gradient's wall trace (the wall
+ * state of the inside trace, a nonlinear function of it) adds a
+ * state-dependent part to K21: for each wall line end the energy row
+ * w = (|m|^2 / (2 rho^2), -m / rho, 1) of the wall state's derivative is
+ * stored with the Jacobian (identity on rho, zero on momentum); the split
+ * matvec and the preconditioner apply it. It is not part of the export.
  */
 int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_t** J, void* stream);
 

@@ -150,6 +150,7 @@ struct ldg_jac {
   void* K11 = nullptr;
   void* K12 = nullptr;
   void* K21 = nullptr;
+  void* Kw = nullptr;     // wall ends: energy row of the wall-state derivative, 2 n_c per line (tiles)
   void* gbuf = nullptr;   // K21 x workspace [E][nc][D][npe] in the vector precision (double)
 };
 

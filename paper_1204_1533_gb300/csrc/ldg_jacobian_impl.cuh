@@ -54,7 +54,7 @@ __device__ __forceinline__ int64_t tile_index(int64_t L, int64_t nk, int64_t k) 
 template <int D, int P, int NC, int EQ, typename R>
 __global__ void __launch_bounds__(Shape<D, P>::THREADS)
     k_jacobian(const double* __restrict__ U, const double* __restrict__ Q, R* __restrict__ K11,
-               R* __restrict__ K12, Geo g, Tab tab, PhysArgs ph) {
+               R* __restrict__ K12, R* __restrict__ Kw, Geo g, Tab tab, PhysArgs ph) {
   using S = Shape<D, P>;
   using T = Dual<R, 1>;
   constexpr int N = S::N, NPE = S::NPE, NQ = S::NQ, NCD = NC * D;
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
   // end data
   int32_t nb[2];
   int swv[2];
+  bool wall[2];
   R nv[2][D], nn[2], uin[2][NC], uo[2][NC];
   R qin[2][VISC ? NCD : 1], qo[2][VISC ? NCD : 1];
 #pragma unroll
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
     const int aend = b0 + end * P * st;
     nb[end] = g.nbr[L * 2 + end];
     swv[end] = g.sw[(e * D + d) * 2 + end];
+    wall[end] = nb[end] < 0 && ph.bck[-1 - nb[end]] == BC_WALL;
     R s = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -133,6 +135,33 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
       if constexpr (VISC) {
 #pragma unroll
         for (int cb = 0; cb < NCD; ++cb) qo[end][cb] = R(0);
+      }
+    }
+  }
+
+  // the gradient's trace at a no-slip wall is the wall state of the inside
+  // trace: its derivative is the identity on rho, zero on momentum, and the
+  // energy row w = (|m|^2 / (2 rho^2), -m / rho, 1); w is stored per line end
+  // (zero at other ends) for the K21 part of the split product
+  if constexpr (VISC && NC == D + 2) {
+    if (Kw) {
+#pragma unroll
+      for (int end = 0; end < 2; ++end) {
+        R w[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[c] = R(0);
+        if (wall[end]) {
+          const R rho = uin[end][0];
+          R m2 = R(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) m2 += uin[end][1 + a] * uin[end][1 + a];
+          w[0] = m2 / (R(2) * rho * rho);
+#pragma unroll
+          for (int a = 0; a < D; ++a) w[1 + a] = -uin[end][1 + a] / rho;
+          w[NC - 1] = R(1);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Kw[tile_index(L, 2 * NC, end * NC + c)] = w[c];
       }
     }
   }
@@ -213,6 +242,35 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
             const R pen = (R)ph.C11 * nn[end];
 #pragma unroll
             for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
+          }
+        } else if (wall[end]) {
+          // no-slip adiabatic wall: pressure flux, viscous momentum flux of
+          // the wall state, momentum penalty; no outside trace
+          if (side == 1) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
+          } else if constexpr (NC != D + 2) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
+          } else {
+            T m2 = ui[1] * ui[1];
+#pragma unroll
+            for (int a = 1; a < D; ++a) m2 = m2 + ui[1 + a] * ui[1 + a];
+            const T pr = R(ph.gamma - 1.0) * (ui[D + 1] - R(0.5) * m2 / ui[0]);
+            F[0] = D1<R>::cst(R(0));
+#pragma unroll
+            for (int a = 0; a < D; ++a) F[1 + a] = pr * nv[end][a];
+            F[D + 1] = D1<R>::cst(R(0));
+            if constexpr (VISC) {
+              T ub[NC], qq[NCD], fv[NC];
+              wall_state<D, T, R>(ui, ub);
+#pragma unroll
+              for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
+              viscous_flux_n<EQ, D, T, R>(ub, qq, nv[end], pp, fv);
+              const R pen = (R)ph.C11b * nn[end];
+#pragma unroll
+              for (int a = 0; a < D; ++a) F[1 + a] = F[1 + a] + fv[1 + a] + pen * (ui[1 + a] - ub[1 + a]);
+            }
           }
         } else {
           // Dirichlet data: the outside trace is g_D, constant
@@ -302,7 +360,19 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
         const int jn = end * P;
         const bool outside = nb[end] >= 0 && swv[end] == 1;
         R fv[NC];
-        viscous_flux_n<EQ, D, R, R>(outside ? uo[end] : uin[end], unit, nv[end], pp, fv);
+        bool walled = false;
+        if constexpr (NC == D + 2) {
+          if (wall[end]) {
+            // the wall's viscous flux: wall state, momentum components only
+            R ub[NC];
+            wall_state<D, R, R>(uin[end], ub);
+            viscous_flux_n<EQ, D, R, R>(ub, unit, nv[end], pp, fv);
+            fv[0] = R(0);
+            fv[NC - 1] = R(0);
+            walled = true;
+          }
+        }
+        if (!walled) viscous_flux_n<EQ, D, R, R>(outside ? uo[end] : uin[end], unit, nv[end], pp, fv);
         if (!outside) {
 #pragma unroll
           for (int i = 0; i < N; ++i) {
@@ -390,7 +460,7 @@ __global__ void k_build_k21(R* __restrict__ K21, Geo g, Tab tab, int64_t NL) {
 }
 
 template <int D, int P, int EQ, typename R>
-cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, R* K11, R* K12,
+cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, R* K11, R* K12, R* Kw,
                          cudaStream_t st) {
   using S = Shape<D, P>;
   constexpr int NC = NComp<EQ, D>::value;
@@ -400,7 +470,7 @@ cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, 
   cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
-  kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, K11, K12, h->geo(), h->tab, h->phys);
+  kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, K11, K12, Kw, h->geo(), h->tab, h->phys);
   count_launch();
   return cudaGetLastError();
 }

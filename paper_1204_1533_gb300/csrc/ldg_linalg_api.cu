@@ -24,7 +24,8 @@ namespace ldg {
   } while (0)
 
 bool ops_supported(const ldg_handle* h) {
-  if (h->p < 1 || h->p > 4 || h->has_wall) return false;
+  if (h->p < 1 || h->p > 4) return false;
+  if (h->has_wall && h->kind != LDG_EQ_EULER && h->kind != LDG_EQ_NAVIER_STOKES) return false;
   if (h->D == 2) return true;
   return h->kind == LDG_EQ_EULER || h->kind == LDG_EQ_NAVIER_STOKES;
 }
@@ -75,6 +76,7 @@ extern "C" int ldg_jac_destroy(ldg_jac_t* J) {
   cudaFree(J->K11);
   cudaFree(J->K12);
   cudaFree(J->K21);
+  cudaFree(J->Kw);
   cudaFree(J->gbuf);
   delete J;
   return LDG_OK;
@@ -99,6 +101,7 @@ extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_
       if (err == cudaSuccess) err = cudaMalloc(&J->K21, rows * h->nk21() * esize(prec));
       if (err == cudaSuccess) err = cudaMemset(J->K21, 0, rows * h->nk21() * esize(prec));
       if (err == cudaSuccess) err = cudaMalloc(&J->gbuf, (size_t)h->ndof * h->D * sizeof(double));
+      if (err == cudaSuccess && h->has_wall) err = cudaMalloc(&J->Kw, rows * 2 * h->nc * esize(prec));
     }
     if (err != cudaSuccess) {
       ldg_jac_destroy(J);

@@ -17,7 +17,8 @@ namespace ldg {
 
 template <int D, int P, int NC, typename R, typename V>
 __global__ void __launch_bounds__(Shape<D, P>::THREADS)
-    k_k21_apply(const R* __restrict__ K21, const V* __restrict__ x, V* __restrict__ gout, Geo g) {
+    k_k21_apply(const R* __restrict__ K21, const R* __restrict__ Kw, const V* __restrict__ x,
+                V* __restrict__ gout, Geo g, Tab tab) {
   using S = Shape<D, P>;
   constexpr int N = S::N, NPE = S::NPE;
   constexpr int tile = NC * NPE, gt = NC * D * NPE;
@@ -71,6 +72,35 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
           for (int j = 0; j < N; ++j) s += (V)kin[i][j][b] * xl[j];
           go[(c * D + b) * NPE + b0 + i * st] = s;
         }
+    }
+    // no-slip wall ends: the trace is the wall state of the end node, whose
+    // derivative keeps rho, drops the momentum and maps to the energy row w
+    if (Kw) {
+#pragma unroll
+      for (int end = 0; end < 2; ++end) {
+        if (g.nbr[L * 2 + end] >= 0) continue;
+        R w[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[c] = Kw[tile_index(L, 2 * NC, end * NC + c)];
+        if (w[NC - 1] == R(0)) continue;  // a Dirichlet end
+        const int aend = b0 + end * P * st;
+        V xa[NC], sE = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          xa[c] = sx[le * tile + c * NPE + aend];
+          sE += (V)w[c] * xa[c];
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const V li = (V)(g.invJ[e * NPE + b0 + i * st] * (end ? tab.L1[i] : tab.L0[i]));
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            const V cf = li * (V)g.nend[(L * 2 + end) * D + b];
+            go[(0 * D + b) * NPE + b0 + i * st] += cf * xa[0];
+            go[((NC - 1) * D + b) * NPE + b0 + i * st] += cf * sE;
+          }
+        }
+      }
     }
   }
   __syncthreads();
@@ -273,8 +303,8 @@ struct PcTables {
 template <int D, int P, int NC, bool VISC, typename R>
 __global__ void __launch_bounds__(256)
     k_precond(const R* __restrict__ K11, const R* __restrict__ K12, const R* __restrict__ K21,
-              R* __restrict__ F, R* __restrict__ Dinv, Geo g, PcTables pt, double shift,
-              double scale) {
+              const R* __restrict__ Kw, R* __restrict__ F, R* __restrict__ Dinv, Geo g, Tab tab, PcTables pt,
+              double shift, double scale) {
   using S = Shape<D, P>;
   constexpr int N = S::N, NPE = S::NPE, NL = S::NL, W = D * P + 1, NCD = NC * D, BB = NC * NC;
   constexpr int64_t NK11 = (N * N + 2 * N) * NC * NC;
@@ -380,6 +410,54 @@ __global__ void __launch_bounds__(256)
                  K21[tile_index(Lo, NK21, N * N * D + tpos * D + b)];
           const int nk = b0 + end * P * st;
           accs[slot_s[ni * NPE + nk]] += v;
+        }
+      }
+      // paths through a no-slip wall end: row i -> q at node t of one of its
+      // lines (K12) -> the wall trace of the end node aw of t's line in a
+      // direction with a wall end (rho kept, energy row w of the wall state)
+      if (Kw) {
+#pragma unroll 1
+        for (int d = 0; d < D; ++d) {
+          const int st = S::stride(d);
+          const int i = idx[d];
+          const int b0 = ni - i * st;
+          const int l = (b0 % st) + (b0 / (st * N)) * st;
+          const int64_t L = (e * D + d) * NL + l;
+#pragma unroll 1
+          for (int t = 0; t < N; ++t) {
+            const int ng = b0 + t * st;
+            R kr[D], ke[D];
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+              kr[b] = K12[tile_index(L, NK12, ((i * N + t) * NC + c) * NCD + 0 * D + b)];
+              ke[b] = K12[tile_index(L, NK12, ((i * N + t) * NC + c) * NCD + (NC - 1) * D + b)];
+            }
+            const int gi[3] = {ng % N, (ng / N) % N, ng / (N * N)};
+#pragma unroll 1
+            for (int dw = 0; dw < D; ++dw) {
+              const int stw = S::stride(dw), pw = gi[dw];
+              const int b0w = ng - pw * stw;
+              const int lw = (b0w % stw) + (b0w / (stw * N)) * stw;
+              const int64_t Lw = (e * D + dw) * NL + lw;
+#pragma unroll 1
+              for (int endw = 0; endw < 2; ++endw) {
+                if (g.nbr[Lw * 2 + endw] >= 0) continue;
+                if (Kw[tile_index(Lw, 2 * NC, endw * NC + NC - 1)] == R(0)) continue;  // Dirichlet end
+                const int aw = b0w + endw * P * stw;
+                const int s = slot_s[ni * NPE + aw];
+                if (s < 0) continue;
+                const R wc = Kw[tile_index(Lw, 2 * NC, endw * NC + cp)];
+                const R li = (R)(g.invJ[e * NPE + ng] * (endw ? tab.L1[pw] : tab.L0[pw]));
+                R v = 0;
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                  const R cf = li * (R)g.nend[(Lw * 2 + endw) * D + b];
+                  v += ((cp == 0 ? kr[b] : R(0)) + ke[b] * wc) * cf;
+                }
+                accs[s] += v;
+              }
+            }
+          }
         }
       }
 #pragma unroll
@@ -634,7 +712,7 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
 }
 
 template <int D, int P, int EQ, typename R, typename V>
-cudaError_t run_jacvec(const ldg_handle* h, const R* K11, const R* K12, const R* K21, V* gbuf,
+cudaError_t run_jacvec(const ldg_handle* h, const R* K11, const R* K12, const R* K21, const R* Kw, V* gbuf,
                        double shift, double scale, const V* x, V* y, cudaStream_t st) {
   using S = Shape<D, P>;
   constexpr int NC = NComp<EQ, D>::value;
@@ -646,7 +724,7 @@ cudaError_t run_jacvec(const ldg_handle* h, const R* K11, const R* K12, const R*
     auto k1 = k_k21_apply<D, P, NC, R, V>;
     err = set_smem_once(k1, sm1);
     if (err != cudaSuccess) return err;
-    k1<<<(unsigned)blocks, S::THREADS, sm1, st>>>(K21, x, gbuf, h->geo());
+    k1<<<(unsigned)blocks, S::THREADS, sm1, st>>>(K21, Kw, x, gbuf, h->geo(), h->tab);
     count_launch();
   }
   const size_t sm2 = (size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0) + D * NC * S::NPE) * sizeof(V);
@@ -677,8 +755,8 @@ size_t precond_smem() {
 }
 
 template <int D, int P, int EQ, typename R>
-cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R* K21, R* F, R* Dinv,
-                        double shift, double scale, cudaStream_t st) {
+cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R* K21, const R* Kw, R* F,
+                        R* Dinv, double shift, double scale, cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
   constexpr bool VISC = IsViscous<EQ>::value;
   const size_t smem = precond_smem<D, P, EQ, R>();
@@ -686,7 +764,8 @@ cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R
   auto kern = k_precond<D, P, NC, VISC, R>;
   cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
-  kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, F, Dinv, h->geo(), pc_tables(h), shift, scale);
+  kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, Kw, F, Dinv, h->geo(), h->tab, pc_tables(h), shift,
+                                           scale);
   count_launch();
   return cudaGetLastError();
 }

@@ -28,11 +28,12 @@ template <int D, int EQ>
 cudaError_t Ops<D, EQ>::jacobian(const ldg_handle* h, const double* U, const double* Q, ldg_jac* J,
                                  cudaStream_t st) {
   if (J->prec == LDG_PREC_FP32) {
-#define F(P) return run_jacobian<D, P, EQ, float>(h, U, Q, (float*)J->K11, (float*)J->K12, st)
+#define F(P) return run_jacobian<D, P, EQ, float>(h, U, Q, (float*)J->K11, (float*)J->K12, (float*)J->Kw, st)
     LDG_FOR_P(F)
 #undef F
   } else {
-#define F(P) return run_jacobian<D, P, EQ, double>(h, U, Q, (double*)J->K11, (double*)J->K12, st)
+#define F(P) \
+  return run_jacobian<D, P, EQ, double>(h, U, Q, (double*)J->K11, (double*)J->K12, (double*)J->Kw, st)
     LDG_FOR_P(F)
 #undef F
   }
@@ -59,22 +60,22 @@ cudaError_t Ops<D, EQ>::jacvec(const ldg_handle* h, const ldg_jac* J, double shi
   if (J->prec == LDG_PREC_FP32 && vprec == LDG_PREC_FP32) {
 #define F(P)                                                                                      \
   return run_jacvec<D, P, EQ, float, float>(h, (const float*)J->K11, (const float*)J->K12,         \
-                                            (const float*)J->K21, (float*)J->gbuf, shift, scale, \
-                                            (const float*)x, (float*)y, st)
+                                            (const float*)J->K21, (const float*)J->Kw,            \
+                                            (float*)J->gbuf, shift, scale, (const float*)x, (float*)y, st)
     LDG_FOR_P(F)
 #undef F
   } else if (J->prec == LDG_PREC_FP32) {
 #define F(P)                                                                                        \
   return run_jacvec<D, P, EQ, float, double>(h, (const float*)J->K11, (const float*)J->K12,          \
-                                             (const float*)J->K21, (double*)J->gbuf, shift, scale, \
-                                             (const double*)x, (double*)y, st)
+                                             (const float*)J->K21, (const float*)J->Kw,             \
+                                             (double*)J->gbuf, shift, scale, (const double*)x, (double*)y, st)
     LDG_FOR_P(F)
 #undef F
   } else if (vprec == LDG_PREC_FP64) {
 #define F(P)                                                                                          \
   return run_jacvec<D, P, EQ, double, double>(h, (const double*)J->K11, (const double*)J->K12,         \
-                                              (const double*)J->K21, (double*)J->gbuf, shift, scale, \
-                                              (const double*)x, (double*)y, st)
+                                              (const double*)J->K21, (const double*)J->Kw,              \
+                                              (double*)J->gbuf, shift, scale, (const double*)x, (double*)y, st)
     LDG_FOR_P(F)
 #undef F
   }
@@ -103,15 +104,15 @@ cudaError_t Ops<D, EQ>::precond(const ldg_handle* h, const ldg_jac* J, double sh
   if (J->prec == LDG_PREC_FP32) {
 #define F(PP)                                                                                   \
   return run_precond<D, PP, EQ, float>(h, (const float*)J->K11, (const float*)J->K12,           \
-                                       (const float*)J->K21, (float*)P->F, (float*)P->Dinv, shift, \
-                                       scale, st)
+                                       (const float*)J->K21, (const float*)J->Kw, (float*)P->F,    \
+                                       (float*)P->Dinv, shift, scale, st)
     LDG_FOR_P(F)
 #undef F
   } else {
 #define F(PP)                                                                                       \
   return run_precond<D, PP, EQ, double>(h, (const double*)J->K11, (const double*)J->K12,            \
-                                        (const double*)J->K21, (double*)P->F, (double*)P->Dinv, shift, \
-                                        scale, st)
+                                        (const double*)J->K21, (const double*)J->Kw, (double*)P->F,    \
+                                        (double*)P->Dinv, shift, scale, st)
     LDG_FOR_P(F)
 #undef F
   }
