@@ -47,10 +47,6 @@ cudaError_t launch_jacvec(const ldg_handle* h, const ldg_jac* J, double shift, d
   LDG_DISPATCH(h, jacvec(h, J, shift, scale, x, y, vprec, st));
   return cudaErrorInvalidValue;
 }
-static size_t precond_smem(const ldg_handle* h, int prec) {
-  LDG_DISPATCH(h, precond_smem(h->p, prec));
-  return 0;
-}
 cudaError_t launch_precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                            ldg_pc* P, cudaStream_t st) {
   LDG_DISPATCH(h, precond(h, J, shift, scale, P, st));
@@ -162,7 +158,6 @@ extern "C" int ldg_precond(ldg_handle_t* h, const ldg_jac_t* J, double shift, do
                            void* stream) {
   if (!h || !J || !Pp || J->h != h) return LDG_ERR_ARG;
   if (!J->built) return LDG_ERR_NOT_BUILT;
-  if (precond_smem(h, J->prec) > 227 * 1024) return LDG_ERR_UNSUPPORTED;
   ldg_pc* P = *Pp;
   if (P && (P->h != h || P->prec != J->prec)) return LDG_ERR_ARG;
   if (!P) {

@@ -300,11 +300,14 @@ struct PcTables {
   const int32_t* lptr;  // [levels + 1]
 };
 
-template <int D, int P, int NC, bool VISC, typename R>
+// INPLACE: the element block is assembled and factored directly in its
+// slice of F / Dinv in global memory (L2-resident while the block works on
+// it) when it does not fit in shared memory (FP64 at 3-D, p = 4).
+template <int D, int P, int NC, bool VISC, typename R, bool INPLACE>
 __global__ void __launch_bounds__(256)
     k_precond(const R* __restrict__ K11, const R* __restrict__ K12, const R* __restrict__ K21,
-              const R* __restrict__ Kw, R* __restrict__ F, R* __restrict__ Dinv, Geo g, Tab tab, PcTables pt,
-              double shift, double scale) {
+              const R* __restrict__ Kw, R* F, R* Dinv, Geo g, Tab tab, PcTables pt, double shift,
+              double scale) {
   using S = Shape<D, P>;
   constexpr int N = S::N, NPE = S::NPE, NL = S::NL, W = D * P + 1, NCD = NC * D, BB = NC * NC;
   constexpr int64_t NK11 = (N * N + 2 * N) * NC * NC;
@@ -312,9 +315,10 @@ __global__ void __launch_bounds__(256)
   constexpr int64_t NK21 = (N * N + N) * D;
   constexpr int OFF12 = N * N * NC * NCD;
   extern __shared__ unsigned char smraw[];
-  R* A = reinterpret_cast<R*>(smraw);            // [NPE][W][NC][NC]
-  R* Di = A + NPE * W * BB;                        // [NPE][NC][NC]
-  R* K21e = Di + NPE * BB;                         // [NPE][W][D] element part of K21
+  R* const sm = reinterpret_cast<R*>(smraw);
+  R* A = INPLACE ? F + (int64_t)blockIdx.x * NPE * W * BB : sm + NPE * W * D;  // [NPE][W][NC][NC]
+  R* Di = INPLACE ? Dinv + (int64_t)blockIdx.x * NPE * BB : A + NPE * W * BB;   // [NPE][NC][NC]
+  R* K21e = sm;                                    // [NPE][W][D] element part of K21
   __shared__ int16_t pat_s[NPE * W];
   __shared__ int8_t slot_s[NPE * NPE];
   __shared__ int16_t lvl_s[NPE];
@@ -510,8 +514,10 @@ __global__ void __launch_bounds__(256)
       __syncthreads();
     }
   }
-  for (int k = tid; k < NPE * W * BB; k += nt) F[e * NPE * W * BB + k] = A[k];
-  for (int k = tid; k < NPE * BB; k += nt) Dinv[e * NPE * BB + k] = Di[k];
+  if constexpr (!INPLACE) {
+    for (int k = tid; k < NPE * W * BB; k += nt) F[e * NPE * W * BB + k] = A[k];
+    for (int k = tid; k < NPE * BB; k += nt) Dinv[e * NPE * BB + k] = Di[k];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -746,6 +752,8 @@ inline PcTables pc_tables(const ldg_handle* h) {
   return t;
 }
 
+// dynamic shared memory of the preconditioner build with the element block
+// staged on chip, and the static tables it adds
 template <int D, int P, int EQ, typename R>
 size_t precond_smem() {
   constexpr int NC = NComp<EQ, D>::value;
@@ -753,19 +761,35 @@ size_t precond_smem() {
   constexpr int W = D * P + 1;
   return (size_t)(S::NPE * W * NC * NC + S::NPE * NC * NC + S::NPE * W * D) * sizeof(R);
 }
+template <int D, int P>
+constexpr size_t precond_static_smem() {
+  using S = Shape<D, P>;
+  constexpr int W = D * P + 1;
+  return (size_t)S::NPE * W * 2 + (size_t)S::NPE * S::NPE + (size_t)S::NPE * 2 + (D * P + 2) * 4 + 64;
+}
 
 template <int D, int P, int EQ, typename R>
 cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R* K21, const R* Kw, R* F,
                         R* Dinv, double shift, double scale, cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
   constexpr bool VISC = IsViscous<EQ>::value;
+  constexpr int W = D * P + 1;
   const size_t smem = precond_smem<D, P, EQ, R>();
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  auto kern = k_precond<D, P, NC, VISC, R>;
-  cudaError_t err = set_smem_once(kern, smem);
-  if (err != cudaSuccess) return err;
-  kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, Kw, F, Dinv, h->geo(), h->tab, pc_tables(h), shift,
-                                           scale);
+  cudaError_t err;
+  if (smem + precond_static_smem<D, P>() <= 227 * 1024) {
+    auto kern = k_precond<D, P, NC, VISC, R, false>;
+    err = set_smem_once(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, Kw, F, Dinv, h->geo(), h->tab, pc_tables(h), shift,
+                                             scale);
+  } else {
+    const size_t sm_in = (size_t)Shape<D, P>::NPE * W * D * sizeof(R);
+    auto kern = k_precond<D, P, NC, VISC, R, true>;
+    err = set_smem_once(kern, sm_in);
+    if (err != cudaSuccess) return err;
+    kern<<<(unsigned)h->E, 256, sm_in, st>>>(K11, K12, K21, Kw, F, Dinv, h->geo(), h->tab, pc_tables(h), shift,
+                                              scale);
+  }
   count_launch();
   return cudaGetLastError();
 }

@@ -14,7 +14,6 @@ struct Ops {
   static cudaError_t k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st);
   static cudaError_t jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                             const void* x, void* y, int vprec, cudaStream_t st);
-  static size_t precond_smem(int p, int prec);
   static cudaError_t precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                              ldg_pc* P, cudaStream_t st);
   static cudaError_t apply(const ldg_handle* h, const ldg_pc* P, const void* r, void* z, int vprec,

@@ -83,22 +83,6 @@ cudaError_t Ops<D, EQ>::jacvec(const ldg_handle* h, const ldg_jac* J, double shi
 }
 
 template <int D, int EQ>
-size_t Ops<D, EQ>::precond_smem(int p, int prec) {
-  const bool f = prec == LDG_PREC_FP32;
-  switch (p) {
-    case 1:
-      return f ? ldg::precond_smem<D, 1, EQ, float>() : ldg::precond_smem<D, 1, EQ, double>();
-    case 2:
-      return f ? ldg::precond_smem<D, 2, EQ, float>() : ldg::precond_smem<D, 2, EQ, double>();
-    case 3:
-      return f ? ldg::precond_smem<D, 3, EQ, float>() : ldg::precond_smem<D, 3, EQ, double>();
-    case 4:
-      return f ? ldg::precond_smem<D, 4, EQ, float>() : ldg::precond_smem<D, 4, EQ, double>();
-  }
-  return 0;
-}
-
-template <int D, int EQ>
 cudaError_t Ops<D, EQ>::precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                                 ldg_pc* P, cudaStream_t st) {
   if (J->prec == LDG_PREC_FP32) {
