@@ -47,11 +47,11 @@ void timer_end(int slot, cudaStream_t st) {
   if (slot >= 0 && 2 * (size_t)slot + 1 < g_kt.pool.size()) cudaEventRecord(g_kt.pool[2 * slot + 1], st);
 }
 
-// The dynamic shared-memory limit is a per-function, per-device attribute:
-// set it the first time a (kernel, device) pair needs more than the default,
-// and afterwards only when a launch asks for more than was set before.
+// The dynamic shared-memory limit is a per-function, per-device attribute
+// (its default leaves 48 KB minus the kernel's static shared memory): set it
+// the first time a (kernel, device) pair is launched, and afterwards only
+// when a launch asks for more than was set before.
 cudaError_t smem_attr_cached(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, size_t> done;
   int dev = 0;

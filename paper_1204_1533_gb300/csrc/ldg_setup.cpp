@@ -18,6 +18,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "ldg_internal.h"
@@ -408,7 +410,6 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
   // residual cancels large flux values against each other, so rounding of
   // the metric terms (coordinates of size L against spacings h) is amplified
   // by about L/h times the flux-to-residual ratio.
-  std::vector<ld> Gn((size_t)npe * 9);
   auto cof_col = [D](const ld* G, int d, ld* nd) {
     // column d of J G^-T; G[a*3+b] = dx_a/dX_b
     if (D == 2) {
@@ -431,7 +432,12 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
   std::vector<ld> xq, wq, phi, dphi;
   gauss01(nq, xq, wq);
   barycentric(s, xq, phi, dphi);
-  for (int64_t e = 0; e < E; ++e) {
+  // elements are independent: the loop runs on the host's cores (long double
+  // is emulated in software on some hosts), every element computed the same way
+  std::atomic<bool> bad{false};
+  auto metric_range = [&](int64_t e_begin, int64_t e_end) {
+  std::vector<ld> Gn((size_t)npe * 9);
+  for (int64_t e = e_begin; e < e_end && !bad.load(std::memory_order_relaxed); ++e) {
     const double* X = mesh->nodes + e * npe * D;
     // G at the nodes: dx_x/dX_b by the nodal derivative matrix along b
     std::fill(Gn.begin(), Gn.end(), (ld)0);
@@ -470,8 +476,8 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
         J = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
             G[2] * (G[3] * G[7] - G[4] * G[6]);
       if (!(J > 0)) {
-        delete h;
-        return LDG_ERR_MESH;
+        bad = true;
+        return;
       }
       invJ[e * npe + a] = (double)(1 / J);
     }
@@ -506,6 +512,23 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
           for (int x = 0; x < D; ++x) nend[(L * 2 + end) * D + x] = (double)(end ? nd[x] : -nd[x]);
         }
       }
+  }
+  };
+  {
+    unsigned nth = std::thread::hardware_concurrency();
+    nth = nth < 1 ? 1 : (nth > 64 ? 64 : nth);
+    if ((int64_t)nth > E) nth = (unsigned)(E > 0 ? E : 1);
+    const int64_t chunk = (E + nth - 1) / nth;
+    std::vector<std::thread> pool;
+    for (unsigned k = 0; k < nth; ++k) {
+      const int64_t e0 = (int64_t)k * chunk, e1 = e0 + chunk < E ? e0 + chunk : E;
+      if (e0 < e1) pool.emplace_back(metric_range, e0, e1);
+    }
+    for (auto& th : pool) th.join();
+  }
+  if (bad) {
+    delete h;
+    return LDG_ERR_MESH;
   }
   *hp = h;
   return LDG_OK;
