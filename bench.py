@@ -12,6 +12,10 @@ precision is FP64; the mixed-precision step (FP32 Jacobian/ILU/Krylov,
 FP64 residual/update/refinement) is timed on the same data beside it.
 
 value = DOF advanced per second over the whole job (all ranks).
+Beside it (rank 0, one GPU): the paper's DIRK3 step on the same workload;
+the 32^3, p=3 Navier-Stokes Taylor-Green vortex and the 64x32x32, p=4
+walled channel at full size (kernels against the HBM roofline, one BDF2
+level in mixed precision and in FP64); the learned Newton guess at 16^3.
 `--impl reference` times the CPU oracle (the only other implementation of
 the method) on a bounded sample of the same workload.
 """
@@ -399,6 +403,8 @@ def gpu_arm(args):
         out["tgv"] = tgv_section(args, hbm)
     if rank == 0 and ws == 1 and not args.no_learned:
         out["learned"] = learned_section(args)
+    if rank == 0 and ws == 1 and not args.no_channel:
+        out["channel"] = channel_section(args, hbm)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -522,6 +528,81 @@ def tgv_section(args, hbm):
     return out
 
 
+def channel_section(args, hbm):
+    """3-D Navier-Stokes channel with sinusoidal bump walls (no-slip,
+    adiabatic), 64 x 32 x 32 curved hexes with wall-normal stretching 1.1,
+    p = 4 (41M DOF), Re = 5000, Mach 0.3: the kernels at full size, then one
+    BDF2 level at CFL 50 (dt from the smallest node spacing and |u| + c) in
+    mixed precision and in FP64 from the same BDF1 start level."""
+    import numpy as np
+    import torch
+
+    from paper_1204_1533_gb300 import inputs as I
+    from paper_1204_1533_gb300 import ldg
+    nx, ny, nz = args.channel
+    m = I.channel_mesh(nx, ny, nz, 4)
+    U0 = I.channel_state(m)
+    eq = {"kind": "ns", "gamma": 1.4, "flux": "roe", "mu": 1.0 / 5000.0, "Pr": 0.72, "bc": {1: "wall"}}
+    t0 = time.perf_counter()
+    h = ldg.ldg_setup(m, eq)
+    t_setup = time.perf_counter() - t0
+    Xr = m["nodes"].reshape(m["nodes"].shape[0], 5, 5, 5, 3)
+    dmin = min(float(np.linalg.norm(np.diff(Xr, axis=ax), axis=-1).min()) for ax in (1, 2, 3))
+    dt = args.channel_cfl * dmin / (1.0 + 1.0 / 0.3)
+    del Xr
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    Ut = torch.from_numpy(U0).cuda()
+    R = torch.empty_like(Ut)
+    out = {"workload": f"ns3d_channel_bump_{nx}x{ny}x{nz}_p4_bdf2_cfl{args.channel_cfl:g}", "dof": h.ndof,
+           "setup_s": t_setup, "dt": dt}
+    k = {}
+    _nvtx(torch, "channel_kernels")
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_residual(h, Ut, R), 3)
+    k["residual_fp64"] = {"ms": t, "dof_s": h.ndof / (t * 1e-3)}
+    J = ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32)
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_jacobian(h, Ut, ldg.PREC_FP32, J), 2)
+    jb = jac_bytes(h, 4)
+    k["jacobian_fp32"] = {"ms": t, "dof_s": h.ndof / (t * 1e-3), "gbs": jb / (t * 1e-3) / 1e9,
+                          "frac_hbm": jb / (t * 1e-3) / 1e9 / hbm}
+    x = torch.randn(h.ndof, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_jacvec(h, J, 1.0, -dt, x, y, ldg.PREC_FP32), 3)
+    vb = jacvec_bytes(h, 4, 4)
+    k["jacvec_fp32"] = {"ms": t, "gbs": vb / (t * 1e-3) / 1e9, "frac_hbm": vb / (t * 1e-3) / 1e9 / hbm}
+    P = ldg.ldg_precond(h, J, 1.0, -2.0 / 3.0 * dt)
+    t = _kernel_ms(torch, flush, lambda: ldg.ldg_precond_apply(h, P, x, y, ldg.PREC_FP32), 3)
+    ab = apply_bytes(h, 4, 4)
+    k["precond_apply_fp32"] = {"ms": t, "gbs": ab / (t * 1e-3) / 1e9, "frac_hbm": ab / (t * 1e-3) / 1e9 / hbm}
+    _nvtx(torch, None)
+    out["kernels"] = k
+    del J, P, x, y
+    torch.cuda.empty_cache()
+    Un = torch.from_numpy(U0).cuda()
+    U1 = torch.empty_like(Un)
+    s1 = ldg.ldg_newton_step(h, U1, Un, None, None, dt, ldg.solver_opts(mode=ldg.MODE_MIXED, first_step=True))
+    out["bdf1_start"] = {"newton_its": s1["newton_its"], "gmres_its": s1["gmres_its"]}
+    sol = {}
+    for name, mode in (("mixed", ldg.MODE_MIXED), ("fp64", ldg.MODE_FP64)):
+        U2 = torch.empty_like(Un)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s = ldg.ldg_newton_step(h, U2, U1, Un, None, dt, ldg.solver_opts(mode=mode, force_rebuild=True))
+        e1.record()
+        e1.synchronize()
+        sol[name] = U2
+        out[name] = {"ms_per_step": e0.elapsed_time(e1), "newton_its": s["newton_its"], "gmres_its": s["gmres_its"],
+                     "res_final_rel": s["res_final"] / s["res0"],
+                     "phases_ms": {q: s[q] for q in ("t_residual_ms", "t_jacobian_ms", "t_precond_ms",
+                                                     "t_linear_ms")}}
+        torch.cuda.empty_cache()
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["rel_diff_mixed_vs_fp64"] = float((sol["mixed"] - sol["fp64"]).norm() / sol["fp64"].norm())
+    del h, sol, Ut, R, Un, U1
+    torch.cuda.empty_cache()
+    return out
+
+
 def learned_section(args):
     """The learned Newton guess on the Taylor-Green vortex at 16^3, p = 3:
     trajectories from the implicit solver for Re ~ U[400, 1600], GPU
@@ -589,6 +670,9 @@ def main():
     ap.add_argument("--tgv-n", type=int, default=32)
     ap.add_argument("--tgv-dt", type=float, default=0.05)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess section")
+    ap.add_argument("--no-channel", action="store_true", help="skip the 3-D walled channel section")
+    ap.add_argument("--channel", type=int, nargs=3, default=[64, 32, 32])
+    ap.add_argument("--channel-cfl", type=float, default=50.0)
     ap.add_argument("--learn-n", type=int, default=16)
     ap.add_argument("--learn-dt", type=float, default=0.03)
     ap.add_argument("--learn-traj", type=int, default=24)
