@@ -348,6 +348,22 @@ int ldg_dirk3_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt
  */
 int ldg_rk4_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt, void* stream);
 
+/*
+ * Steady state by pseudo-time continuation (Sec. 4.1): n_steps backward
+ * Euler steps with increasing time steps dt_k = dt0 growth^k, each solved
+ * by the Newton-GMRES solver of ldg_newton_step, then a final step without
+ * the time derivative (R(U) = 0, solved as a backward Euler step with
+ * dt = 1e15, for which (I - dt A) is dt A up to rounding). U: device FP64
+ * [ndof], in: the initial state, out: the steady state. opts as in
+ * ldg_newton_step (first_step and predictor are ignored; the start of every
+ * step is the previous level); stats: counts and phase times summed over
+ * the steps, res0 / res_final those of the final step (norms of dt R).
+ * Work buffers shared with ldg_dirk3_step. Synchronises on stream. Errors
+ * as ldg_newton_step; LDG_ERR_ARG for dt0 <= 0, growth < 1 or n_steps < 0.
+ */
+int ldg_steady_solve(ldg_handle_t* h, double* U, double dt0, double growth, int32_t n_steps,
+                     const ldg_solver_opts_t* opts, ldg_step_stats_t* stats, void* stream);
+
 /* ---- learned Newton predictor (not in the paper) ------------------------
  * A line-local MLP n_in -> 128 -> 128 -> 128 -> n_out with GELU (tanh form)
  * predicts, for every line of reference direction 1, the correction to the

@@ -686,6 +686,43 @@ extern "C" int ldg_dirk3_step(ldg_handle_t* h, double* U, const double* Un, doub
   return LDG_OK;
 }
 
+// Pseudo-time continuation to a steady state (Sec. 4.1): backward Euler with
+// growing steps, then R(U) = 0 as a backward Euler step with dt = 1e15.
+extern "C" int ldg_steady_solve(ldg_handle_t* h, double* U, double dt0, double growth, int32_t n_steps,
+                                const ldg_solver_opts_t* o, ldg_step_stats_t* stats, void* stream) {
+  if (!h || !U || !o || !stats || !(dt0 > 0) || !(growth >= 1.0) || n_steps < 0) return LDG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->ndof;
+  if (!h->dirk) LDG_CUDA_TRY(cudaMalloc((void**)&h->dirk, 5 * (size_t)n * sizeof(double)));
+  double* Uprev = h->dirk + 3 * n;
+  *stats = ldg_step_stats_t{};
+  double dt = dt0;
+  for (int k = 0; k <= n_steps; ++k) {
+    const double dtk = k < n_steps ? dt : 1e15;
+    LDG_CUDA_TRY(cudaMemcpyAsync(Uprev, U, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ldg_solver_opts_t ok = *o;
+    ok.first_step = 1;
+    ok.predictor = LDG_PRED_EXTRAP;  // start from the previous level
+    if (k > 0) ok.force_rebuild = 0;
+    ldg_step_stats_t sk;
+    const int rc = ldg_newton_step(h, U, Uprev, nullptr, nullptr, dtk, &ok, &sk, stream);
+    if (rc) return rc;
+    stats->newton_its += sk.newton_its;
+    stats->gmres_its += sk.gmres_its;
+    stats->jac_builds += sk.jac_builds;
+    stats->refine_sweeps += sk.refine_sweeps;
+    stats->t_residual_ms += sk.t_residual_ms;
+    stats->t_jacobian_ms += sk.t_jacobian_ms;
+    stats->t_precond_ms += sk.t_precond_ms;
+    stats->t_linear_ms += sk.t_linear_ms;
+    stats->res0 = sk.res0;
+    stats->res_final = sk.res_final;
+    stats->res_pred = sk.res_pred;
+    dt *= growth;
+  }
+  return LDG_OK;
+}
+
 // Classical RK4 (Sec. 4.1, explicit time-stepping).
 extern "C" int ldg_rk4_step(ldg_handle_t* h, double* U, const double* Un, double dt, void* stream) {
   if (!h || !U || !Un || !(dt > 0)) return LDG_ERR_ARG;

@@ -104,6 +104,8 @@ _SIGS = {
                         C.POINTER(ldg_step_stats_t), _P],
     "ldg_dirk3_step": [_P, _P, _P, C.c_double, C.POINTER(ldg_solver_opts_t), C.POINTER(ldg_step_stats_t), _P],
     "ldg_rk4_step": [_P, _P, _P, C.c_double, _P],
+    "ldg_steady_solve": [_P, _P, C.c_double, C.c_double, C.c_int32, C.POINTER(ldg_solver_opts_t),
+                         C.POINTER(ldg_step_stats_t), _P],
 }
 
 
@@ -377,6 +379,13 @@ def ldg_dirk3_step(h, U_next, U_n, dt, opts, stream=None):
 
 def ldg_rk4_step(h, U_next, U_n, dt, stream=None):
     _check(lib().ldg_rk4_step(h.ptr, _dptr(U_next), _dptr(U_n), float(dt), _stream(stream)), "ldg_rk4_step")
+
+
+def ldg_steady_solve(h, U, dt0, growth, n_steps, opts, stream=None):
+    st = ldg_step_stats_t()
+    _check(lib().ldg_steady_solve(h.ptr, _dptr(U), float(dt0), float(growth), int(n_steps), C.byref(opts),
+                                  C.byref(st), _stream(stream)), "ldg_steady_solve")
+    return st.as_dict()
 
 
 def paper_policy_opts(mode=MODE_FP64, rtol=1e-8, max_newton=50):

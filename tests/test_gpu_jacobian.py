@@ -376,3 +376,54 @@ def test_rk4_vortex_convergence_on_gpu(L):
         errs.append(np.abs(U.cpu().numpy() - exact).max())
     rate = math.log2(errs[0] / errs[1])
     assert rate > 3.7, (errs, rate)      # the oracle's run of this study gives 4.1
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_poisson_steady_solve_and_rates(L, mode):
+    """Configuration 1 on the GPU: -lap u = f on the perturbed unit square,
+    p = 3, solved by the steady driver (one step without the time
+    derivative); the solution matches the oracle's direct solve, and the
+    error falls at the rate of the paper's Table 2 (p + 1)."""
+    import scipy.sparse.linalg as spla
+    import torch
+    errs = []
+    for n in (4, 8, 16):
+        m = I.poisson_square_mesh(n, 3)
+        f = I.poisson_source(m)
+        gD = np.zeros_like(f)
+        eq = {"kind": "poisson", "C11b": 1.0, "bc": {0: "dirichlet"}, "gD": gD, "source": f}
+        h = L.ldg_setup(m, eq)
+        U = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+        st = L.ldg_steady_solve(h, U, 1.0, 1.0, 0, L.solver_opts(mode=mode, rtol=1e-12, max_newton=20))
+        assert st["res_final"] <= 1e-12 * st["res0"]
+        Ug = U.cpu().numpy()
+        errs.append(np.abs(Ug - I.poisson_exact(m)).max())
+        if n == 4:
+            disc = Discretization(m, {"kind": "poisson", "C11b": 1.0, "bc": {0: "dirichlet"}})
+            A = JAC.A_full(disc, np.zeros_like(f), gD, f)
+            Uo = spla.spsolve(A.tocsc(), -full_residual(disc, np.zeros_like(f), gD, f).ravel()).reshape(f.shape)
+            assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+    gold = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                                 "poisson_rates.txt"), comments="#")
+    rate = math.log2(errs[1] / errs[2])
+    assert abs(rate - gold[2][3]) < 0.6, (errs, rate)       # p = 3, last refinement: 4.0
+
+
+def test_steady_continuation_euler(L):
+    """Pseudo-time continuation on a compressible case: a perturbed uniform
+    flow in a box whose boundary data is that uniform flow; backward Euler
+    with growing steps, then the step without the time derivative, drive the
+    residual to the target and the state to the uniform flow."""
+    import torch
+    m = I.structured_mesh((4, 4), 2, (0.0, 0.0), (4.0, 4.0), (False, False), perturb=0.1)
+    g = I.vortex_state(m, eps=0.0)
+    eq = dict(EULER, bc={0: "dirichlet"}, gD=g)
+    h = L.ldg_setup(m, eq)
+    U = torch.from_numpy(I.smooth_perturbation(m, g, 0.02, periods=[4, 4])).cuda()
+    R = torch.empty_like(U)
+    L.ldg_residual(h, U, R)
+    r0 = float(R.abs().max())
+    st = L.ldg_steady_solve(h, U, 0.1, 2.0, 10, L.solver_opts(mode=0, max_newton=30))
+    L.ldg_residual(h, U, R)
+    assert float(R.abs().max()) <= 1e-6 * r0, (r0, float(R.abs().max()), st)
+    assert float((U - torch.from_numpy(g).cuda()).abs().max()) <= 1e-6 * float(np.abs(g).max())
