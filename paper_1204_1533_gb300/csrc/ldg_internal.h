@@ -117,9 +117,6 @@ struct ldg_handle {
   size_t ws_bytes = 0;
   double* Qbuf = nullptr;    // LDG gradient of the last residual [E][nc][D][npe]
   double* dirk = nullptr;    // DIRK3 stage vectors K1..K3, B, U_i [5][ndof]
-  double* hpin = nullptr;    // pinned host slots of the GMRES Hessenberg columns [(m+1)][(m+2)]
-  int hpin_m = 0;
-  std::vector<cudaEvent_t> gev;  // one event per GMRES iteration
   double* red = nullptr;     // reduction scratch (doubles)
   int64_t red_len = 0;
   ldg::Geo geo() const {

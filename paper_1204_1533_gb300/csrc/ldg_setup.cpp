@@ -651,8 +651,6 @@ extern "C" int ldg_destroy(ldg_handle_t* h) {
   cudaFree(h->src);
   cudaFree(h->Qbuf);
   cudaFree(h->dirk);
-  if (h->hpin) cudaFreeHost(h->hpin);
-  for (cudaEvent_t ev : h->gev) cudaEventDestroy(ev);
   cudaFree(h->red);
   cudaFree(h->nbf);
   cudaFree(h->linemet);

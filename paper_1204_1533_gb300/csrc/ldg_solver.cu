@@ -335,43 +335,8 @@ static cudaError_t cgs2(const V* Vb, int kv, int64_t n, V* w, const Work& ws, cu
   return ortho<V, OrthoOp::Dots>(w, 1, n, w, nullptr, ws.part, ws.hacc + kv, nullptr, st);
 }
 
-// v *= 1 / sqrt(hsq[0]) when hsq[0] > 0 (the Arnoldi normalisation, on the
-// device so that the next iteration needs no host round trip)
-template <typename V>
-__global__ void k_norm_scale(V* __restrict__ v, const double* __restrict__ hsq, int64_t n) {
-  const double s = hsq[0];
-  if (!(s > 0.0)) return;
-  const double inv = 1.0 / sqrt(s);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = (V)(inv * (double)v[i]);
-}
-
-// pinned host slots for the per-iteration Hessenberg columns and one event
-// per iteration, kept with the handle
-static int gmres_host_buffers(ldg_handle* h, int m) {
-  if (h->hpin_m < m) {
-    if (h->hpin) cudaFreeHost(h->hpin);
-    h->hpin = nullptr;
-    h->hpin_m = 0;
-    if (cudaMallocHost((void**)&h->hpin, (size_t)(m + 1) * (m + 2) * sizeof(double)) != cudaSuccess)
-      return LDG_ERR_CUDA;
-    h->hpin_m = m;
-  }
-  while ((int)h->gev.size() < m) {
-    cudaEvent_t ev;
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return LDG_ERR_CUDA;
-    h->gev.push_back(ev);
-  }
-  return LDG_OK;
-}
-
 // Right-preconditioned GMRES(m) on (I - adt A) x = b for vectors of type V;
-// b is overwritten; x receives the solution (zero initial guess). The host
-// keeps the Hessenberg matrix and its Givens rotations one iteration behind
-// the device: iteration k is enqueued (basis vector normalised on the
-// device, its coefficients copied to pinned slot k) before the host reads
-// iteration k-1's coefficients, so the GPU never waits for the host; when
-// k-1 meets the tolerance, the already enqueued iteration k is discarded.
+// b is overwritten; x receives the solution (zero initial guess).
 template <typename V>
 static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double tol, int m, Work& w,
                  int* its_out, double* rel_out, cudaStream_t st) {
@@ -379,9 +344,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
   V* Vb = (V*)w.Vb;
   V* z = (V*)w.z;
   V* t = (V*)w.t;
-  int rc = gmres_host_buffers(h, m);
-  if (rc) return rc;
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(m + 2);
   // beta = ||b||
   if (mdot<V>(b, 1, n, b, w.part, w.hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
   double bb = 0;
@@ -400,36 +363,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
   g[0] = beta;
   int k_used = 0;
   double rel = 1.0;
-  // host part of iteration j: Hessenberg column, rotations, residual estimate;
-  // 1 = converged (or happy breakdown), 0 = continue, < 0 = error
-  auto process = [&](int j) -> int {
-    if (cudaEventSynchronize(h->gev[j]) != cudaSuccess) return LDG_ERR_CUDA;
-    const double* hc = h->hpin + (size_t)j * (m + 2);
-    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
-    const double hn = std::sqrt(hc[j + 1]);
-    if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
-    H[(size_t)(j + 1) * m + j] = hn;
-    for (int i = 0; i < j; ++i) {
-      const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-      H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-      H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
-    }
-    const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-    const double den = std::hypot(a, c);
-    if (den == 0.0) return LDG_ERR_GMRES_BREAKDOWN;
-    cs[j] = a / den;
-    sn[j] = c / den;
-    H[(size_t)j * m + j] = den;
-    H[(size_t)(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    k_used = j + 1;
-    rel = std::fabs(g[j + 1]) / beta;
-    return (rel <= tol || hn == 0.0) ? 1 : 0;
-  };
-  int k = 0;
-  bool stop = false;
-  for (; k < m && !stop; ++k) {
+  for (int k = 0; k < m; ++k) {
     V* vk = Vb + (int64_t)k * n;
     V* vn = Vb + (int64_t)(k + 1) * n;
     if (launch_precond_apply(h, h->Pn, vk, z, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
@@ -437,20 +371,31 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
     // classical Gram-Schmidt, twice
     LDG_CUDA_TRY(cudaMemsetAsync(w.hacc, 0, (k + 2) * sizeof(double), st));
     if (cgs2<V>(Vb, k + 1, n, vn, w, st) != cudaSuccess) return LDG_ERR_CUDA;
-    LDG_CUDA_TRY(cudaMemcpyAsync(h->hpin + (size_t)k * (m + 2), w.hacc, (k + 2) * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
-    k_norm_scale<V><<<grid_for(n), 256, 0, st>>>(vn, w.hacc + k + 1, n);
+    LDG_CUDA_TRY(cudaMemcpyAsync(hc.data(), w.hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LDG_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
+    const double hn = std::sqrt(hc[k + 1]);
+    if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
+    H[(size_t)(k + 1) * m + k] = hn;
+    if (hn > 0) k_scale_to<V, V><<<grid_for(n), 256, 0, st>>>(vn, vn, 1.0 / hn, n);
     count_launch();
-    LDG_CUDA_TRY(cudaEventRecord(h->gev[k], st));
-    if (k >= 1) {
-      const int r = process(k - 1);
-      if (r < 0) return r;
-      stop = r == 1;
+    for (int j = 0; j < k; ++j) {
+      const double a = H[(size_t)j * m + k], c = H[(size_t)(j + 1) * m + k];
+      H[(size_t)j * m + k] = cs[j] * a + sn[j] * c;
+      H[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * c;
     }
-  }
-  if (!stop) {
-    const int r = process(k - 1);
-    if (r < 0) return r;
+    const double a = H[(size_t)k * m + k], c = H[(size_t)(k + 1) * m + k];
+    const double den = std::hypot(a, c);
+    if (den == 0.0) return LDG_ERR_GMRES_BREAKDOWN;
+    cs[k] = a / den;
+    sn[k] = c / den;
+    H[(size_t)k * m + k] = den;
+    H[(size_t)(k + 1) * m + k] = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    k_used = k + 1;
+    rel = std::fabs(g[k + 1]) / beta;
+    if (rel <= tol || hn == 0.0) break;
   }
   std::vector<double> yv(k_used);
   for (int i = k_used - 1; i >= 0; --i) {
