@@ -349,15 +349,16 @@ int ldg_dirk3_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt
 int ldg_rk4_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt, void* stream);
 
 /*
- * Steady state by pseudo-time continuation (Sec. 4.1): n_steps backward
- * Euler steps with increasing time steps dt_k = dt0 growth^k, each solved
- * by the Newton-GMRES solver of ldg_newton_step, then a final step without
- * the time derivative (R(U) = 0, solved as a backward Euler step with
- * dt = 1e15, for which (I - dt A) is dt A up to rounding). U: device FP64
+ * Steady state by pseudo-time continuation (Sec. 4.1): up to n_steps
+ * backward Euler steps with increasing time steps dt_k = dt0 growth^k, each
+ * solved by the Newton-GMRES solver of ldg_newton_step, then a final step
+ * without the time derivative (R(U) = 0, solved as a backward Euler step
+ * with dt = 1e15, for which (I - dt A) is dt A up to rounding), stopping as
+ * soon as ||R(U)||_2 <= opts->rtol ||R(U_initial)||_2. U: device FP64
  * [ndof], in: the initial state, out: the steady state. opts as in
- * ldg_newton_step (first_step and predictor are ignored; the start of every
- * step is the previous level); stats: counts and phase times summed over
- * the steps, res0 / res_final those of the final step (norms of dt R).
+ * ldg_newton_step (first_step and predictor are ignored; every step starts
+ * from the previous level); stats: counts and phase times summed over the
+ * steps, res0 = ||R(U_initial)||_2, res_final = ||R(U)||_2 at return.
  * Work buffers shared with ldg_dirk3_step. Synchronises on stream. Errors
  * as ldg_newton_step; LDG_ERR_ARG for dt0 <= 0, growth < 1 or n_steps < 0.
  */

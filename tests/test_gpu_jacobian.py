@@ -424,6 +424,7 @@ def test_steady_continuation_euler(L):
     L.ldg_residual(h, U, R)
     r0 = float(R.abs().max())
     st = L.ldg_steady_solve(h, U, 0.1, 2.0, 10, L.solver_opts(mode=0, max_newton=30))
+    assert st["res_final"] <= 1e-8 * st["res0"], st
     L.ldg_residual(h, U, R)
     assert float(R.abs().max()) <= 1e-6 * r0, (r0, float(R.abs().max()), st)
     assert float((U - torch.from_numpy(g).cuda()).abs().max()) <= 1e-6 * float(np.abs(g).max())
