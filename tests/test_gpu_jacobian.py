@@ -423,7 +423,9 @@ def test_steady_continuation_euler(L):
     R = torch.empty_like(U)
     L.ldg_residual(h, U, R)
     r0 = float(R.abs().max())
-    st = L.ldg_steady_solve(h, U, 0.1, 2.0, 10, L.solver_opts(mode=0, max_newton=30))
+    # dt 0.1 .. 25.6 then the step without the time derivative (beyond
+    # dt ~ 50 the backward Euler Newton stalls here, in the oracle too)
+    st = L.ldg_steady_solve(h, U, 0.1, 2.0, 9, L.solver_opts(mode=0, max_newton=50))
     assert st["res_final"] <= 1e-8 * st["res0"], st
     L.ldg_residual(h, U, R)
     assert float(R.abs().max()) <= 1e-6 * r0, (r0, float(R.abs().max()), st)
