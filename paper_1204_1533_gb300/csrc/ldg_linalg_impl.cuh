@@ -571,13 +571,13 @@ __device__ __forceinline__ V group_sum(V v, V* scratch, int lane) {
     for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
   } else {
-    scratch[lane] = v;
-    __syncwarp();
+    // gather the G values of the group by shuffles (idle lanes past the last
+    // full group read wrapped lanes; their result is not used)
+    (void)scratch;
     const int g0 = lane - lane % G;
     V s = 0;
 #pragma unroll
-    for (int k = 0; k < G; ++k) s += scratch[g0 + k];
-    __syncwarp();
+    for (int k = 0; k < G; ++k) s += __shfl_sync(0xffffffffu, v, (g0 + k) & 31);
     return s;
   }
 }
