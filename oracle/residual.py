@@ -19,6 +19,11 @@ Numerical fluxes (Sec. 3, Eqs. 25-28, C12 = n S/2, C22 = 0):
   Dirichlet boundary (Eqs. 27-28):
       F^vis . n = F^vis(u_in, q_in) . n + C11_b |n| (u_in - g_D),  u^ = g_D,
       inviscid part: the Riemann flux with outside trace g_D.
+  Neumann boundary (Eqs. 29-30 with C22 = 0): the prescribed flux enters as
+  a flux vector G at the boundary nodes (data gN[E, nc, D, npe]; a scalar
+  normal flux g_N is G = g_N n/|n|), so that a node where two Neumann faces
+  meet carries one datum for both:
+      F^ . n = G . n (n the non-unit normal of the line end),  u^ = u_in.
   No-slip adiabatic wall (Navier-Stokes; not in the paper):
       inviscid part: pressure-only flux (0, p_in n, 0),
       u^ = (rho_in, 0, 0, 0, rho E_in - |rho v_in|^2 / (2 rho_in)),
@@ -56,6 +61,7 @@ class Discretization:
         self.C11 = float(eq.get("C11", 0.0))
         self.C11b = float(eq.get("C11b", 1.0))
         self.bc = dict(eq.get("bc", {0: "dirichlet"}))
+        self.gN = None if eq.get("gN") is None else np.asarray(eq["gN"], dtype=np.float64)
 
     @property
     def ndof(self):
@@ -131,6 +137,8 @@ def gradient(disc, U, gD=None):
                         uhat = np.where(m, gd, uhat)
                     elif kind == "wall":
                         uhat = np.where(m, _wall_state(u_in, D), uhat)
+                    elif kind == "neumann":
+                        uhat = np.where(m, u_in, uhat)
                     else:
                         raise ValueError(f"unknown boundary kind {kind!r}")
             nend = disc.met.nplus[d] if end == 1 else disc.met.nminus[d]   # [E, nl, D]
@@ -199,6 +207,8 @@ def residual(disc, U, Q=None, gD=None, source=None):
                                 + disc.C11b * ph.norm(n) * (u_in - gd)
                     elif kind == "wall":
                         Fb = _wall_flux(disc, u_in, q_in if visc else None, n)
+                    elif kind == "neumann":
+                        Fb = _lead(_neumann_flux(disc, sid, n), len(lead))
                     else:
                         raise ValueError(f"unknown boundary kind {kind!r}")
                     Fh = np.where(m, Fb, Fh)
@@ -220,6 +230,14 @@ def _gather_q(Q, g):
     gg = np.where(g >= 0, g, 0)
     out = flat[..., gg, :, :]                        # [..., *g.shape, nc, D]
     return np.moveaxis(np.moveaxis(out, -2, 0), -1, 1)
+
+
+def _neumann_flux(disc, sid, n):
+    """G . n at the line-end nodes sid [E, nl] (zero without data): [nc, E, nl]."""
+    if disc.gN is None:
+        return np.zeros((disc.nc,) + sid.shape)
+    G = _gather_q(disc.gN, sid)                       # [nc, D, E, nl]
+    return sum(G[:, a] * n[a] for a in range(disc.D))
 
 
 def _wall_flux(disc, u_in, q_in, n):

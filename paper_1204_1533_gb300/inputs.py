@@ -222,6 +222,193 @@ def permute_nodal(field, maps):
 
 
 # ---------------------------------------------------------------------------
+# unstructured meshes (non-grid topology: vertices of valence 3, 5, 6, ...)
+# ---------------------------------------------------------------------------
+def _multilinear(cpos, s, D):
+    """Node coordinates [(p+1)^D, D] of the multilinear element with corner
+    positions cpos [2^D, D] (local corner c at reference corner bits of c)."""
+    p = len(s) - 1
+    npe = (p + 1) ** D
+    ref = np.array([[s[(a // (p + 1) ** b) % (p + 1)] for b in range(D)] for a in range(npe)])
+    w = np.ones((npe, 1 << D))
+    for c, bits in enumerate(_corner_bits(D)):
+        for d in range(D):
+            w[:, c] *= ref[:, d] if bits[d] else (1.0 - ref[:, d])
+    return w @ cpos
+
+
+def _grid_vertices(n, D, L, periodic, perturb, rng):
+    """Perturbed vertex grid: (ids [...], positions [..., D]) indexed by the
+    unwrapped integer grid point; periodic images share ids and offsets."""
+    nv = n if periodic else n + 1
+    h = L / n
+    delta = rng.uniform(-1.0, 1.0, size=(nv,) * D + (D,)) * perturb * h
+    if not periodic:
+        inner = np.zeros((nv,) * D, dtype=bool)
+        inner[(slice(1, nv - 1),) * D] = True
+        delta[~inner] = 0.0
+
+    def vid(g):
+        w = [int(v) % nv if periodic else int(v) for v in g]
+        out = 0
+        for d in reversed(range(D)):
+            out = out * nv + w[d]
+        return out
+
+    def pos(g):
+        w = tuple(int(v) % nv if periodic else int(v) for v in g)
+        return np.array([g[d] * h for d in range(D)], dtype=np.float64) + delta[w[::-1]]
+    return vid, pos, nv ** D
+
+
+def _finish_mesh(D, p, s, corners_list, lo, hi, periodic):
+    """Mesh dictionary from elements given as (vertex ids [2^D], corner
+    positions [2^D, D]); faces seen once get boundary tag 0."""
+    E = len(corners_list)
+    npe = (p + 1) ** D
+    nodes = np.zeros((E, npe, D))
+    verts = np.zeros((E, 1 << D), dtype=np.int64)
+    for e, (ids, cpos) in enumerate(corners_list):
+        verts[e] = ids
+        nodes[e] = _multilinear(np.asarray(cpos), s, D)
+    count = {}
+    for e in range(E):
+        for f in range(2 * D):
+            d, end = divmod(f, 2)
+            key = tuple(sorted(int(verts[e, c]) for c in range(1 << D) if ((c >> d) & 1) == end))
+            count[key] = count.get(key, 0) + 1
+    btag = -np.ones((E, 2 * D), dtype=np.int32)
+    for e in range(E):
+        for f in range(2 * D):
+            d, end = divmod(f, 2)
+            key = tuple(sorted(int(verts[e, c]) for c in range(1 << D) if ((c >> d) & 1) == end))
+            if count[key] == 1:
+                btag[e, f] = 0
+    return {"D": D, "p": int(p), "s": s, "nodes": np.ascontiguousarray(nodes), "vertices": verts,
+            "btag": btag, "periodic": (bool(periodic),) * D, "lo": tuple(lo), "hi": tuple(hi)}
+
+
+def unstructured_quad_mesh(n=2, p=3, L=1.0, periodic=False, perturb=0.1, refine=0, seed=MESH_SEED):
+    """Unstructured straight-sided quadrilaterals on [0,L]^2.
+
+    An n x n vertex grid (interior vertices, or all vertices when periodic,
+    perturbed by U(-perturb h, perturb h) per coordinate) is split into
+    triangles along a seeded random diagonal per cell; every triangle is
+    split into three quadrilaterals through its edge midpoints and centroid
+    (vertices of valence 3 at the centroids, 4-8 elsewhere). `refine`
+    uniform refinements then split every quadrilateral into four through
+    its edge midpoints and centre, so a refined mesh tiles the same
+    bilinear elements (the nested sequence of a convergence study).
+    6 n^2 4^refine elements. Periodic meshes need n >= 3."""
+    rng = np.random.default_rng(seed)
+    s = gll_nodes(p)
+    vid, pos, nid = _grid_vertices(n, 2, L, periodic, perturb, rng)
+    next_id = [nid]
+    mids = {}
+
+    def mid_id(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mids:
+            mids[key] = next_id[0]
+            next_id[0] += 1
+        return mids[key]
+
+    def fresh():
+        next_id[0] += 1
+        return next_id[0] - 1
+
+    quads = []  # (ids [4] in local corner order, positions [4, 2])
+    for j in range(n):
+        for i in range(n):
+            g = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+            if rng.integers(2):
+                tris = [(g[0], g[1], g[2]), (g[0], g[2], g[3])]
+            else:
+                tris = [(g[0], g[1], g[3]), (g[1], g[2], g[3])]
+            for tri in tris:  # counter-clockwise
+                ids = [vid(v) for v in tri]
+                P = [pos(v) for v in tri]
+                cid = fresh()
+                cen = (P[0] + P[1] + P[2]) / 3.0
+                for k in range(3):
+                    a, b, c = k, (k + 1) % 3, (k + 2) % 3
+                    mab, mca = mid_id(ids[a], ids[b]), mid_id(ids[c], ids[a])
+                    # local corners (0,0) (1,0) (0,1) (1,1): A, m_AB, m_CA, centroid
+                    quads.append(([ids[a], mab, mca, cid],
+                                  np.array([P[a], 0.5 * (P[a] + P[b]), 0.5 * (P[c] + P[a]), cen])))
+    for _ in range(refine):
+        mids = {}
+        finer = []
+        for ids, P in quads:
+            c0, c1, c2, c3 = ids
+            m01, m02, m13, m23 = mid_id(c0, c1), mid_id(c0, c2), mid_id(c1, c3), mid_id(c2, c3)
+            cc = fresh()
+            Q = {"c0": P[0], "c1": P[1], "c2": P[2], "c3": P[3],
+                 "m01": 0.5 * (P[0] + P[1]), "m02": 0.5 * (P[0] + P[2]),
+                 "m13": 0.5 * (P[1] + P[3]), "m23": 0.5 * (P[2] + P[3]), "cc": 0.25 * P.sum(axis=0)}
+            I = {"c0": c0, "c1": c1, "c2": c2, "c3": c3, "m01": m01, "m02": m02, "m13": m13, "m23": m23,
+                 "cc": cc}
+            for kids in (("c0", "m01", "m02", "cc"), ("m01", "c1", "cc", "m13"),
+                         ("m02", "cc", "c2", "m23"), ("cc", "m13", "m23", "c3")):
+                finer.append(([I[k] for k in kids], np.array([Q[k] for k in kids])))
+        quads = finer
+    return _finish_mesh(2, p, s, quads, (0.0, 0.0), (L, L), periodic)
+
+
+def unstructured_hex_mesh(n=3, p=2, L=1.0, periodic=False, perturb=0.0, seed=MESH_SEED):
+    """Unstructured trilinear hexahedra on [0,L]^3: every cell of an n^3
+    vertex grid is split into the six tetrahedra of the Kuhn (Freudenthal)
+    triangulation, which is conforming across cells, and every tetrahedron
+    into four hexahedra, one per tetrahedron vertex, with corners at the
+    vertex, its three edge midpoints, its three face centroids and the
+    tetrahedron's centroid (non-grid topology: edges shared by 3-8
+    hexahedra). 24 n^3 elements. Periodic meshes need n >= 3."""
+    rng = np.random.default_rng(seed)
+    s = gll_nodes(p)
+    vid, pos, nid = _grid_vertices(n, 3, L, periodic, perturb, rng)
+    next_id = [nid]
+    keyed = {}
+
+    def kid(key):
+        if key not in keyed:
+            keyed[key] = next_id[0]
+            next_id[0] += 1
+        return keyed[key]
+
+    hexes = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for perm in itertools.permutations(range(3)):
+                    g = [np.array([i, j, k])]
+                    for ax in perm:
+                        step = np.zeros(3, dtype=int)
+                        step[ax] = 1
+                        g.append(g[-1] + step)
+                    ids = [vid(v) for v in g]
+                    P = [pos(v) for v in g]
+                    tid = kid(("tet", i, j, k, perm))
+                    cen = sum(P) / 4.0
+                    for a in range(4):
+                        o = [b for b in range(4) if b != a]
+                        b1, b2, b3 = o
+                        if np.linalg.det(np.array([P[b1] - P[a], P[b2] - P[a], P[b3] - P[a]])) < 0:
+                            b2, b3 = b3, b2
+
+                        def em(b):
+                            return kid(("e",) + tuple(sorted((ids[a], ids[b]))))
+
+                        def fm(b, c):
+                            return kid(("f",) + tuple(sorted((ids[a], ids[b], ids[c]))))
+                        # local corners by bits (x, y, z): x -> b1, y -> b2, z -> b3
+                        cid = [ids[a], em(b1), em(b2), fm(b1, b2), em(b3), fm(b1, b3), fm(b2, b3), tid]
+                        cp = [P[a], 0.5 * (P[a] + P[b1]), 0.5 * (P[a] + P[b2]), (P[a] + P[b1] + P[b2]) / 3.0,
+                              0.5 * (P[a] + P[b3]), (P[a] + P[b1] + P[b3]) / 3.0, (P[a] + P[b2] + P[b3]) / 3.0, cen]
+                        hexes.append((cid, np.array(cp)))
+    return _finish_mesh(3, p, s, hexes, (0.0, 0.0, 0.0), (L, L, L), periodic)
+
+
+# ---------------------------------------------------------------------------
 # workload meshes (sizes and perturbations of the benchmark configurations)
 # ---------------------------------------------------------------------------
 def poisson_square_mesh(n=8, p=3, perturb=0.15, seed=MESH_SEED):

@@ -30,12 +30,16 @@ def _meshes():
     m3 = I.reorient(I.structured_mesh((3, 3, 3), 2, (0,) * 3, (1,) * 3, (True,) * 3, perturb=0.1))[0]
     mp = I.poisson_square_mesh(4, 3)
     mc = I.channel_mesh(4, 4, 3, 2)
+    mu2 = I.unstructured_quad_mesh(2, 3, perturb=0.15)
+    mu3 = I.unstructured_hex_mesh(3, 2, periodic=True, perturb=0.1)
     return [("vortex2d", m2, EULER), ("box3d", m3, EULER),
             ("poisson", mp, {"kind": "poisson", "bc": {0: "dirichlet"}}),
-            ("channel", mc, {"kind": "ns", "mu": 0.01, "Pr": 0.72, "bc": {1: "wall"}})]
+            ("channel", mc, {"kind": "ns", "mu": 0.01, "Pr": 0.72, "bc": {1: "wall"}}),
+            ("unstructured_quads", mu2, {"kind": "poisson", "bc": {0: "dirichlet"}}),
+            ("unstructured_hexes", mu3, EULER)]
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(6))
 def test_tables_bit_exact_and_metrics_match_oracle(case):
     name, m, eq = _meshes()[case]
     host = ldg.ldg_setup_host(m, eq)
