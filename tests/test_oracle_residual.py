@@ -344,3 +344,37 @@ def test_reduced_jacobian_is_split_product(kind):
     A = JAC.A_full(disc, U, gD)
     S = JAC.K11(disc, U, Q, gD) + JAC.K12(disc, U, Q, gD) @ JAC.K21(disc, gD)
     assert np.abs((A - S).toarray()).max() < 1e-12 * np.abs(A.toarray()).max()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("C11b", [0.1, 10.0])
+def test_poisson_rates_insensitive_to_boundary_penalty(C11b):
+    # the Dirichlet penalty only needs to be positive (Sec. 3): the u-rate
+    # p + 1 of Table 2 holds for penalties two decades apart
+    import scipy.sparse.linalg as spla
+    p, errs = 2, []
+    for n in (4, 8, 16):
+        m = I.poisson_square_mesh(n, p)
+        disc = Discretization(m, dict(POISSON, C11b=C11b))
+        gD = np.zeros((disc.E, 1, disc.npe))
+        f = I.poisson_source(m)
+        A = JAC.A_full(disc, gD, gD, f)
+        U = spla.spsolve(A.tocsc(), -full_residual(disc, gD, gD, f).ravel()).reshape(gD.shape)
+        errs.append(np.abs(U - I.poisson_exact(m)).max())
+    assert abs(math.log2(errs[1] / errs[2]) - (p + 1)) < 0.6, errs
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "mixed"])
+def test_poisson_operator_is_dissipative(bc):
+    # dU/dt = R(U) with R the LDG form of lap u: the dense Jacobian on a tiny
+    # mesh is nonsingular and every eigenvalue has a negative real part (the
+    # semi-discrete heat equation decays), with Dirichlet or mixed sides
+    m = I.reorient(I.structured_mesh((2, 2), 2, (0.0, 0.0), (1.0, 1.0), (False, False), perturb=0.15,
+                                     btag_of_face=(lambda d, end: 1 if end == 1 else 0) if bc == "mixed" else None))[0]
+    eq = dict(POISSON, bc={0: "dirichlet", 1: "neumann"})
+    disc = Discretization(m, eq)
+    gD = np.zeros((disc.E, 1, disc.npe))
+    A = JAC.dense_brute_force(lambda X: full_residual(disc, X.reshape(gD.shape), gD).ravel(), gD.ravel())
+    lam = np.linalg.eigvals(A)
+    assert lam.real.max() < 0.0, lam.real.max()
+    assert np.linalg.cond(A) < 1e8
