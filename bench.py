@@ -67,8 +67,10 @@ def euler_residual_flops(D, p, nc, E):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # the timed kernels from one ncu capture of the unchanged kernel on this
-# workload; None until a capture of the current kernel exists.
-TRAFFIC = {"precond_apply": 125.28e6, "jacvec": None, "gram_schmidt": None}
+# workload (for the Gram-Schmidt sweeps, whose size varies with the basis:
+# the mean over every launch of one timed step); None until a capture of the
+# current kernel exists.
+TRAFFIC = {"precond_apply": 125.28e6, "jacvec": None, "gram_schmidt": 37.28e6}
 
 
 def jac_bytes(h, esz):
@@ -277,7 +279,9 @@ def gpu_arm(args):
     ms_mx, value_mx = job_rate(np.mean(tmx), h.ndof, ws, "cuda")
 
     # ---- end to end through the public API with host buffers ----------------
-    te2e, _ = run(ldg.MODE_FP64, max(2, args.steps // 2), 1, e2e=True)
+    # the same time levels as the device-resident run (same Newton and GMRES
+    # work per step), with the inputs copied in and the result copied out
+    te2e, _ = run(ldg.MODE_FP64, args.steps, args.warmup, e2e=True)
     ms_e2e, value_e2e = job_rate(np.mean(te2e), h.ndof, ws, "cuda")
 
     # ---- the paper's own integrator: DIRK3 on the same workload -------------

@@ -57,6 +57,8 @@ extern "C" {
 
 #define LDG_BC_DIRICHLET 0  /* Eqs. 27-28: u^ = g_D, penalty C11_b        */
 #define LDG_BC_WALL 1       /* no-slip adiabatic wall (NS; builder-defined) */
+#define LDG_BC_NEUMANN 2    /* Eqs. 29-30 (C22 = 0): F^.n = G.n from the
+                               prescribed flux G (g_N below), u^ = u_inside */
 
 #define LDG_PREC_FP32 0
 #define LDG_PREC_FP64 1
@@ -95,6 +97,14 @@ typedef struct {
  *   g_D               [n_elem][n_c][(p+1)^D] Dirichlet data (read at boundary
  *                     face nodes) or NULL
  *   source            [n_elem][n_c][(p+1)^D] source S(x) added to R, or NULL
+ *   g_N               [n_elem][n_c][D][(p+1)^D] prescribed flux vector G at
+ *                     the nodes of Neumann faces, or NULL (zero flux). A line
+ *                     end on a Neumann face takes F^.n = G.n with its
+ *                     non-unit normal n (a scalar normal flux g_N is
+ *                     G = g_N n/|n|); a corner node shared by two Neumann
+ *                     faces carries one vector for both. The flux does not
+ *                     depend on the state, so its Jacobian entries are zero;
+ *                     the gradient's trace there is the inside value.
  */
 typedef struct {
   int32_t kind;
@@ -109,6 +119,7 @@ typedef struct {
   const int32_t* bc_kind;
   const double* g_D;
   const double* source;
+  const double* g_N;
 } ldg_equations_t;
 
 typedef struct ldg_handle ldg_handle_t;

@@ -73,6 +73,7 @@ struct Geo {
   const double* invJ;   // [E][npe]
   const double* gD;     // [E][nc][npe] or null
   const double* src;    // [E][nc][npe] or null
+  const double* gN;     // [E][nc][D][npe] or null (Neumann flux vector)
   int64_t E;
 };
 
@@ -99,6 +100,7 @@ struct ldg_handle {
   double* invJ = nullptr;
   double* gD = nullptr;
   double* src = nullptr;
+  double* gN = nullptr;      // prescribed Neumann flux [E][nc][D][npe]
   int8_t* nbf = nullptr;     // neighbour face id per element face [E][2D] (-1: boundary)
   std::vector<int8_t> nbf_h;
   int16_t* pat = nullptr;    // element Line-DG pattern: sorted columns of each row [npe][Dp+1]
@@ -128,6 +130,7 @@ struct ldg_handle {
     g.invJ = invJ;
     g.gD = gD;
     g.src = src;
+    g.gN = gN;
     g.E = E;
     return g;
   }

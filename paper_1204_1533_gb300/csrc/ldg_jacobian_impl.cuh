@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
   // end data
   int32_t nb[2];
   int swv[2];
-  bool wall[2];
+  bool wall[2], neu[2];
   R nv[2][D], nn[2], uin[2][NC], uo[2][NC];
   R qin[2][VISC ? NCD : 1], qo[2][VISC ? NCD : 1];
 #pragma unroll
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
     nb[end] = g.nbr[L * 2 + end];
     swv[end] = g.sw[(e * D + d) * 2 + end];
     wall[end] = nb[end] < 0 && ph.bck[-1 - nb[end]] == BC_WALL;
+    neu[end] = nb[end] < 0 && ph.bck[-1 - nb[end]] == BC_NEUMANN;
     R s = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -243,6 +244,10 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
 #pragma unroll
             for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
           }
+        } else if (neu[end]) {
+          // Neumann: the prescribed flux does not depend on the state
+#pragma unroll
+          for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
         } else if (wall[end]) {
           // no-slip adiabatic wall: pressure flux, viscous momentum flux of
           // the wall state, momentum penalty; no outside trace
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
           }
         }
         if (!walled) viscous_flux_n<EQ, D, R, R>(outside ? uo[end] : uin[end], unit, nv[end], pp, fv);
-        if (!outside) {
+        if (!outside && !neu[end]) {
 #pragma unroll
           for (int i = 0; i < N; ++i) {
             const R li = tlift<R>(tab, end, i);
@@ -405,10 +410,11 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
 
 // K21 = dQ/dU, scalar and component-independent (Sec. 4.2), built in FP64:
 //   in-line [(i N + j) D + b] = (1/J_i) (-sum_q Kd_iq n_d,b(xi_q) phi_j(xi_q)
-//                               + L_e,i n_e,b [j = end node, interior, S_e = +1])
+//                               + L_e,i n_e,b [j = end node, interior with
+//                                 S_e = +1, or a Neumann boundary end])
 //   face    [N^2 D + i D + b] = (1/J_i) L_e,i n_e,b for the interior end with S_e = -1
 template <int D, int P, typename R>
-__global__ void k_build_k21(R* __restrict__ K21, Geo g, Tab tab, int64_t NL) {
+__global__ void k_build_k21(R* __restrict__ K21, Geo g, Tab tab, PhysArgs ph, int64_t NL) {
   using S = Shape<D, P>;
   constexpr int N = S::N, NPE = S::NPE, NQ = S::NQ;
   constexpr int64_t NK = (N * N + N) * D;
@@ -427,10 +433,12 @@ __global__ void k_build_k21(R* __restrict__ K21, Geo g, Tab tab, int64_t NL) {
 #pragma unroll
     for (int a = 0; a < D; ++a) nv[end][a] = g.nend[(L * 2 + end) * D + a];
   int nb[2], swv[2];
+  bool own[2];  // the end's trace u^ is this line's own end node
 #pragma unroll
   for (int end = 0; end < 2; ++end) {
     nb[end] = g.nbr[L * 2 + end];
     swv[end] = g.sw[(e * D + d) * 2 + end];
+    own[end] = nb[end] >= 0 ? swv[end] == 1 : ph.bck[-1 - nb[end]] == BC_NEUMANN;
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -444,8 +452,7 @@ __global__ void k_build_k21(R* __restrict__ K21, Geo g, Tab tab, int64_t NL) {
         for (int q = 0; q < NQ; ++q) s -= tab.Kd[i][q] * nq[q][b] * tab.Phi[q][j];
 #pragma unroll
         for (int end = 0; end < 2; ++end)
-          if (j == end * P && nb[end] >= 0 && swv[end] == 1)
-            s += (end ? tab.L1[i] : tab.L0[i]) * nv[end][b];
+          if (j == end * P && own[end]) s += (end ? tab.L1[i] : tab.L0[i]) * nv[end][b];
         K21[tile_index(L, NK, (i * N + j) * D + b)] = (R)(ij * s);
       }
 #pragma unroll
@@ -478,7 +485,7 @@ cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, 
 template <int D, int P, typename R>
 cudaError_t run_k21(const ldg_handle* h, R* K21, cudaStream_t st) {
   const int64_t NL = h->nlines();
-  k_build_k21<D, P, R><<<(unsigned)((NL + 127) / 128), 128, 0, st>>>(K21, h->geo(), h->tab, NL);
+  k_build_k21<D, P, R><<<(unsigned)((NL + 127) / 128), 128, 0, st>>>(K21, h->geo(), h->tab, h->phys, NL);
   count_launch();
   return cudaGetLastError();
 }

@@ -22,7 +22,7 @@ namespace ldg {
 
 enum { EQ_POISSON = 0, EQ_EULER = 1, EQ_NS = 2, EQ_ADV = 3 };
 enum { FLUX_ROE = 0, FLUX_LF = 1 };
-enum { BC_DIRICHLET = 0, BC_WALL = 1 };
+enum { BC_DIRICHLET = 0, BC_WALL = 1, BC_NEUMANN = 2 };
 
 struct Phys {
   double gamma, mu, Pr, C11, C11b;

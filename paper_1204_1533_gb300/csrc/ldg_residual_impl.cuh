@@ -95,6 +95,11 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
         }
       } else {
         const int kind = ph.bck[-1 - nb];
+        if (kind == BC_NEUMANN) {  // Eq. 30 with C22 = 0
+#pragma unroll
+          for (int c = 0; c < NC; ++c) uh[end][c] = uin[c];
+          continue;
+        }
         if constexpr (NC == D + 2) {
           if (kind == BC_WALL) {
             wall_state<D, double, double>(uin, uh[end]);
@@ -270,6 +275,17 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
       } else {
         const int kind = ph.bck[-1 - nb];
         bool done = false;
+        if (kind == BC_NEUMANN) {  // Eq. 29: F^.n = G.n from the prescribed flux
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            double s = 0.0;
+            if (g.gN)
+#pragma unroll
+              for (int a = 0; a < D; ++a) s = fma(g.gN[((e * NC + c) * D + a) * NPE + aend], nv[a], s);
+            F[c] = s;
+          }
+          done = true;
+        }
         if constexpr (NC == D + 2) {
           if (kind == BC_WALL) {
             // no-slip adiabatic wall: pressure flux, viscous flux of the wall

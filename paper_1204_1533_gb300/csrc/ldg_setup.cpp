@@ -219,6 +219,8 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
   if (!mesh->s || !mesh->nodes || !mesh->vertices || !mesh->btag) return LDG_ERR_ARG;
   if (eq->kind < 0 || eq->kind > 3) return LDG_ERR_ARG;
   if (eq->n_bc < 0 || eq->n_bc > ldg::MAXBC) return LDG_ERR_ARG;
+  for (int t = 0; t < eq->n_bc && eq->bc_kind; ++t)
+    if (eq->bc_kind[t] < LDG_BC_DIRICHLET || eq->bc_kind[t] > LDG_BC_NEUMANN) return LDG_ERR_ARG;
   if (!ldg::residual_supported(D, p, eq->kind)) return LDG_ERR_UNSUPPORTED;
   const int n = p + 1, npe = ipow(n, D), nl = ipow(n, D - 1);
   // node set: increasing, end points 0 and 1, symmetric
@@ -559,6 +561,8 @@ extern "C" int ldg_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_
     err = up((void**)&h->gD, eq->g_D, (size_t)h->ndof * sizeof(double));
   if (err == cudaSuccess && eq->source)
     err = up((void**)&h->src, eq->source, (size_t)h->ndof * sizeof(double));
+  if (err == cudaSuccess && eq->g_N)
+    err = up((void**)&h->gN, eq->g_N, (size_t)h->ndof * D * sizeof(double));
   if (err == cudaSuccess) err = up((void**)&h->nbf, h->nbf_h.data(), h->nbf_h.size());
   if (err == cudaSuccess) err = up((void**)&h->linemet, linemet.data(), linemet.size() * sizeof(float));
   if (err == cudaSuccess && h->viscous())
@@ -648,6 +652,7 @@ extern "C" int ldg_destroy(ldg_handle_t* h) {
   cudaFree(h->nend);
   cudaFree(h->invJ);
   cudaFree(h->gD);
+  cudaFree(h->gN);
   cudaFree(h->src);
   cudaFree(h->Qbuf);
   cudaFree(h->dirk);

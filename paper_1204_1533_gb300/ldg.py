@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libldg.so")
 
 EQ = {"poisson": 0, "euler": 1, "ns": 2, "advection": 3}
 FLUX = {"roe": 0, "lf": 1}
-BC = {"dirichlet": 0, "wall": 1}
+BC = {"dirichlet": 0, "wall": 1, "neumann": 2}
 PREC_FP32, PREC_FP64 = 0, 1
 MODE_FP64, MODE_MIXED = 0, 1
 PRED_EXTRAP, PRED_GIVEN, PRED_CHECKED = 0, 1, 2
@@ -42,7 +42,8 @@ class ldg_equations_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("flux", C.c_int32), ("gamma", C.c_double),
                 ("mu", C.c_double), ("Pr", C.c_double), ("C11", C.c_double),
                 ("C11_b", C.c_double), ("adv", C.c_double * 3), ("n_bc", C.c_int32),
-                ("bc_kind", C.c_void_p), ("g_D", C.c_void_p), ("source", C.c_void_p)]
+                ("bc_kind", C.c_void_p), ("g_D", C.c_void_p), ("source", C.c_void_p),
+                ("g_N", C.c_void_p)]
 
 
 class ldg_solver_opts_t(C.Structure):
@@ -185,13 +186,20 @@ class _Marshal:
             self.bck[t] = BC[k]
         self.gD = None if eq.get("gD") is None else np.ascontiguousarray(eq["gD"], dtype=np.float64)
         self.src = None if eq.get("source") is None else np.ascontiguousarray(eq["source"], dtype=np.float64)
+        self.gN = None if eq.get("gN") is None else np.ascontiguousarray(eq["gN"], dtype=np.float64)
+        D, npe = int(mesh["D"]), self.nodes.shape[1]
+        nc = D + 2 if eq["kind"] in ("euler", "ns") else 1
+        for name, a, per in (("gD", self.gD, nc), ("source", self.src, nc), ("gN", self.gN, nc * D)):
+            if a is not None and a.size != self.nodes.shape[0] * per * npe:
+                raise ValueError(f"{name}: expected {self.nodes.shape[0] * per * npe} values, got {a.size}")
         adv = list(eq.get("adv", [0.0, 0.0, 0.0])) + [0.0] * 3
         self.eq = ldg_equations_t(
             EQ[eq["kind"]], FLUX[eq.get("flux", "roe")], float(eq.get("gamma", 1.4)),
             float(eq.get("mu", 0.0)), float(eq.get("Pr", 0.72)), float(eq.get("C11", 0.0)),
             float(eq.get("C11b", 1.0)), (C.c_double * 3)(*adv[:3]), nbc, self.bck.ctypes.data,
             None if self.gD is None else self.gD.ctypes.data,
-            None if self.src is None else self.src.ctypes.data)
+            None if self.src is None else self.src.ctypes.data,
+            None if self.gN is None else self.gN.ctypes.data)
 
 
 def ldg_setup_host(mesh, eq):

@@ -85,11 +85,47 @@ def _case(name):
         eq = {"kind": "poisson", "bc": {0: "dirichlet"}, "gD": np.zeros((1, 1, 25)),
               "source": np.ones((1, 1, 25))}
         return m, eq, I.random_state((1, 1, 25))
+    if name == "unstructured_euler2d_p4":
+        m = I.unstructured_quad_mesh(3, 4, L=10.0, periodic=True, perturb=0.15)
+        return m, EULER, I.smooth_perturbation(m, I.vortex_state(m), 0.05, periods=[10, 10])
+    if name == "unstructured_ns2d_p3":
+        m = I.unstructured_quad_mesh(3, 3, L=10.0, periodic=True, perturb=0.15)
+        return m, ns(0.05), I.smooth_perturbation(m, I.vortex_state(m), 0.05, periods=[10, 10])
+    if name == "unstructured_poisson_p3":
+        m = I.unstructured_quad_mesh(2, 3, perturb=0.15, refine=1)
+        E = m["nodes"].shape[0]
+        eq = {"kind": "poisson", "C11b": 1.0, "bc": {0: "dirichlet"},
+              "gD": np.zeros((E, 1, 16)), "source": I.poisson_source(m)}
+        return m, eq, I.poisson_exact(m) * 1.1 + 0.05 * I.random_state((E, 1, 16))
+    if name == "unstructured_ns3d_p2":
+        m = I.unstructured_hex_mesh(3, 2, L=2 * math.pi, periodic=True, perturb=0.1)
+        return m, ns(0.02), I.smooth_perturbation(m, I.tgv_state(m, mach=0.3), 0.05)
+    if name == "unstructured_euler3d_p3_farfield":
+        m = I.unstructured_hex_mesh(1, 3, perturb=0.0)
+        g = _free_stream(m, 5)
+        return m, dict(EULER, bc={0: "dirichlet"}, gD=g), I.smooth_perturbation(m, g, 0.05, periods=[1, 1, 1])
+    if name == "poisson_neumann_p3":
+        m = I.reorient(I.structured_mesh((4, 4), 3, (0.0, 0.0), (1.0, 1.0), (False, False), perturb=0.15,
+                                         btag_of_face=lambda d, end: 1 if end == 1 else 0))[0]
+        E = m["nodes"].shape[0]
+        eq = {"kind": "poisson", "C11b": 1.0, "bc": {0: "dirichlet", 1: "neumann"},
+              "gD": np.zeros((E, 1, 16)), "source": I.poisson_source(m),
+              "gN": -I.poisson_exact_grad(m) + 0.1 * I.random_state((E, 1, 2, 16))}
+        return m, eq, I.poisson_exact(m) * 1.1 + 0.05 * I.random_state((E, 1, 16))
+    if name == "ns2d_neumann_p2":
+        m = I.reorient(I.structured_mesh((3, 3), 2, (0.0, 0.0), (1.0, 1.0), (True, False), perturb=0.1,
+                                         btag_of_face=lambda d, end: 1 if end == 1 else 0))[0]
+        g = _free_stream(m, 4)
+        eq = dict(ns(0.05), bc={0: "dirichlet", 1: "neumann"}, gD=g,
+                  gN=I.random_state((m["nodes"].shape[0], 4, 2, 9), seed=8))
+        return m, eq, I.smooth_perturbation(m, g, 0.05, periods=[1, 1])
     raise KeyError(name)
 
 
 CASES = ["euler2d_p4", "lf2d_p3", "euler3d_p2", "ns3d_tgv_p3", "ns3d_p4", "ns2d_p2_reoriented",
-         "ns3d_p1", "poisson_p3", "advection_p3", "channel_walls_p2", "single_element_poisson"]
+         "ns3d_p1", "poisson_p3", "advection_p3", "channel_walls_p2", "single_element_poisson",
+         "unstructured_euler2d_p4", "unstructured_ns2d_p3", "unstructured_poisson_p3", "unstructured_ns3d_p2",
+         "unstructured_euler3d_p3_farfield", "poisson_neumann_p3", "ns2d_neumann_p2"]
 
 
 def _ext(a):
@@ -125,7 +161,8 @@ def test_residual_matches_oracle(L, name):
     assert err <= RTOL * np.abs(Ro).max(), (name, err, np.abs(Ro).max())
 
 
-@pytest.mark.parametrize("name", ["ns3d_tgv_p3", "ns2d_p2_reoriented", "poisson_p3", "channel_walls_p2"])
+@pytest.mark.parametrize("name", ["ns3d_tgv_p3", "ns2d_p2_reoriented", "poisson_p3", "channel_walls_p2",
+                                  "poisson_neumann_p3", "ns2d_neumann_p2"])
 def test_gradient_matches_oracle(L, name):
     import torch
     m, eq, U = _case(name)
