@@ -107,6 +107,17 @@ def K21(disc, gD=None):
     return colored_jacobian(disc, f, U0, 1)
 
 
+def coupled(disc, U, Q, gD=None, source=None):
+    """Jacobian of the split system (R(U, Q), Q - D(U, Q)) of Eq. 36 with
+    respect to (U, Q): [[K11, K12], [-K21, I - K22]] (Sec. 4.1; K22 != 0
+    when C22 != 0)."""
+    k11 = colored_jacobian(disc, lambda X: residual(disc, X, Q, gD, source), U, 1)
+    k12 = colored_jacobian(disc, lambda X: residual(disc, U, X, gD, source), Q, 1)
+    k21 = colored_jacobian(disc, lambda X: gradient(disc, X, gD, Q), U, 1)
+    k22 = colored_jacobian(disc, lambda X: gradient(disc, U, gD, X), Q, 1)
+    return sp.bmat([[k11, k12], [-k21, sp.eye(Q.size) - k22]]).tocsr()
+
+
 def A_full(disc, U, gD=None, source=None):
     """dR(U, D(U))/dU directly (the reduced Jacobian of Eq. 40)."""
     def f(X):

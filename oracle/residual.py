@@ -19,6 +19,14 @@ Numerical fluxes (Sec. 3, Eqs. 25-28, C12 = n S/2, C22 = 0):
   Dirichlet boundary (Eqs. 27-28):
       F^vis . n = F^vis(u_in, q_in) . n + C11_b |n| (u_in - g_D),  u^ = g_D,
       inviscid part: the Riemann flux with outside trace g_D.
+  Stabilised scheme (C11, C22 != 0, Sec. 3 and Table 2's lower half): at
+  interior ends
+      u^ = (switch value) + C22 (F^vis(inside) - F^vis(outside)) . n/|n|,
+  the sign that makes C22 a penalty on the jump of the normal flux (the
+  printed sign, with the outside as the positive side as the switch form
+  implies, gives an unstable operator); at Neumann ends
+      u^ = u_in + C22 (F^vis(inside) . n/|n| - g_N).
+  D then depends on Q, and a solve couples U and Q (Eq. 36).
   Neumann boundary (Eqs. 29-30 with C22 = 0): the prescribed flux enters as
   a flux vector G at the boundary nodes (data gN[E, nc, D, npe]; a scalar
   normal flux g_N is G = g_N n/|n|), so that a node where two Neumann faces
@@ -60,6 +68,7 @@ class Discretization:
         self.met = Metrics(mesh, self.rules)
         self.C11 = float(eq.get("C11", 0.0))
         self.C11b = float(eq.get("C11b", 1.0))
+        self.C22 = float(eq.get("C22", 0.0))
         self.bc = dict(eq.get("bc", {0: "dirichlet"}))
         self.gN = None if eq.get("gN") is None else np.asarray(eq["gN"], dtype=np.float64)
 
@@ -108,17 +117,28 @@ def _end_traces(disc, U, d, end, uL):
     return u_in, u_out, g
 
 
-def gradient(disc, U, gD=None):
-    """Q = D(U) (Eqs. 19, 20, 26, 28, 32), shape [..., E, nc, D, npe]."""
+def gradient(disc, U, gD=None, Q=None):
+    """Q = D(U) (Eqs. 19, 20, 26, 28, 32), shape [..., E, nc, D, npe]; with
+    C22 != 0 the trace depends on the given Q as well: D(U, Q) of Eq. 36."""
     D, p, r = disc.D, disc.p, disc.rules
-    lead = U.shape[:-3]
-    Q = np.zeros(lead + (disc.E, disc.nc, D, disc.npe), dtype=U.dtype)
+    stab = disc.C22 != 0.0
+    if stab and Q is None:
+        raise ValueError("C22 != 0: the gradient depends on Q")
+    if stab:
+        lead = np.broadcast_shapes(U.shape[:-3], Q.shape[:-4])
+        U = np.broadcast_to(U, lead + U.shape[-3:])
+        Qin = np.broadcast_to(Q, lead + Q.shape[-4:])
+        dtype = np.result_type(U, Qin)
+    else:
+        lead = U.shape[:-3]
+        dtype = U.dtype
+    Q = np.zeros(lead + (disc.E, disc.nc, D, disc.npe), dtype=dtype)
     for d in range(D):
         uL = to_lines(U, D, p, d)                          # [..., E, nc, nl, p+1]
         uq = np.einsum("qi,...i->...q", r.Phi, uL)          # [..., E, nc, nl, nq]
         ng = np.moveaxis(disc.met.ng[d], -1, 0)             # [D, E, nl, nq]
         # b_i = uhat^+ n^+ phi_i(1) + uhat^- n^- phi_i(0) - sum_q w_q u_q n_q phi_i'(xi_q)
-        b = np.zeros(lead + (disc.E, disc.nc, D, disc.nl, p + 1), dtype=U.dtype)
+        b = np.zeros(lead + (disc.E, disc.nc, D, disc.nl, p + 1), dtype=dtype)
         for a in range(D):
             w = uq * ng[a][:, None]                          # [..., E, nc, nl, nq]
             b[..., a, :, :] -= np.einsum("qi,q,...q->...i", r.dPhi, r.wq, w)
@@ -127,6 +147,15 @@ def gradient(disc, U, gD=None):
             Sw = disc.S[:, d, end][:, None]                  # [E, 1]
             uhat = np.where(Sw == 1, u_in, u_out)
             bnd = g < 0
+            nend = disc.met.nplus[d] if end == 1 else disc.met.nminus[d]   # [E, nl, D]
+            if stab:
+                # C22 times the jump of the normal viscous flux (Eq. 26)
+                n = np.moveaxis(nend, -1, 0)                                 # [D, E, nl]
+                q_in = np.moveaxis(np.moveaxis(to_lines(Qin, D, p, d)[..., end * p], -3, 0), -2, 1)
+                sc = ph.norm(n)
+                f_in = ph.viscous_flux_n(disc.eq, u_in, q_in, n) / sc
+                f_out = ph.viscous_flux_n(disc.eq, u_out, _gather_q(Qin, g), n) / sc
+                uhat = uhat + disc.C22 * (f_in - f_out)
             if np.any(bnd):
                 kinds = _bc_kind(disc, g)
                 if gD is not None:
@@ -138,10 +167,14 @@ def gradient(disc, U, gD=None):
                     elif kind == "wall":
                         uhat = np.where(m, _wall_state(u_in, D), uhat)
                     elif kind == "neumann":
-                        uhat = np.where(m, u_in, uhat)
+                        un = u_in
+                        if stab:   # Eq. 30
+                            sid = _self_ids(disc, d, end)
+                            gn = _lead(_neumann_flux(disc, sid, n), len(lead)) / sc
+                            un = u_in + disc.C22 * (f_in - gn)
+                        uhat = np.where(m, un, uhat)
                     else:
                         raise ValueError(f"unknown boundary kind {kind!r}")
-            nend = disc.met.nplus[d] if end == 1 else disc.met.nminus[d]   # [E, nl, D]
             for a in range(D):
                 contrib = np.moveaxis(uhat * nend[..., a], 0, -2)          # [..., E, nc, nl]
                 b[..., a, :, end * p] += contrib
@@ -257,6 +290,12 @@ def _wall_flux(disc, u_in, q_in, n):
         pen[D + 1] = 0.0 * pen[D + 1]
         F = F + Fv + pen
     return F
+
+
+def coupled_residual(disc, U, Q, gD=None, source=None):
+    """The split system of Eq. 36 as one residual: (R(U, Q), Q - D(U, Q)),
+    zero at a steady solution; with C22 != 0 the two parts are coupled."""
+    return residual(disc, U, Q, gD, source), Q - gradient(disc, U, gD, Q)
 
 
 def full_residual(disc, U, gD=None, source=None):
