@@ -261,18 +261,23 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     clk = Clocks(local)
     l0 = ldg.ldg_launch_count()
-    t64, s64 = run(ldg.MODE_FP64, args.steps, args.warmup, live=True)
+    t64, s64 = run(ldg.MODE_FP64, args.steps, args.warmup)
     launches = (ldg.ldg_launch_count() - l0)
     clocks = clk.stop()
     torch.cuda.synchronize()
-    # device time and algorithmic work of the Krylov kernels inside the timed
-    # steps: (launches, ms, bytes, FLOPs) summed over the timed launches
+    ms, value = job_rate(np.mean(t64), h.ndof, ws, "cuda")
+    launches_per_step = launches / (args.steps + args.warmup + 1)
+    # the same steps again with every apply, matvec and Gram-Schmidt launch
+    # bracketed by CUDA events on its stream (the brackets cost about 1 ms a
+    # step, so these steps are not the ones `value` is taken from): device
+    # time and algorithmic work, (launches, ms, bytes, FLOPs) summed over the
+    # timed launches
+    run(ldg.MODE_FP64, args.steps, args.warmup, live=True)
+    torch.cuda.synchronize()
     live = {name: ldg.ldg_kernel_timer_read(k, ldg.PREC_FP64)
             for name, k in (("precond_apply", ldg.KT_APPLY), ("jacvec", ldg.KT_JACVEC),
                             ("gram_schmidt", ldg.KT_ORTHO))}
     ldg.ldg_kernel_timer(False)
-    ms, value = job_rate(np.mean(t64), h.ndof, ws, "cuda")
-    launches_per_step = launches / (args.steps + args.warmup + 1)
 
     # ---- mixed-precision steps on the same data ----------------------------
     tmx, smx = run(ldg.MODE_MIXED, args.steps, args.warmup)
@@ -409,6 +414,8 @@ def gpu_arm(args):
         out["learned"] = learned_section(args)
     if rank == 0 and ws == 1 and not args.no_channel:
         out["channel"] = channel_section(args, hbm)
+    if rank == 0 and ws == 1 and not args.no_stabilized:
+        out["stabilized"] = stabilized_section(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -607,6 +614,56 @@ def channel_section(args, hbm):
     return out
 
 
+def stabilized_section(args):
+    """The stabilised LDG scheme (C11 = C22 = 1/20) of Table 2's lower half on
+    configuration 1's finest mesh (16 x 16 perturbed quads, p = 3): the
+    coupled (U, Q) solve with its element block-Jacobi preconditioner, the
+    D(U, Q) kernel, and the errors against the manufactured solution next to
+    the minimal-dissipation solve of the same mesh."""
+    import numpy as np
+    import torch
+
+    from paper_1204_1533_gb300 import inputs as I
+    from paper_1204_1533_gb300 import ldg
+    m = I.poisson_square_mesh(16, 3)
+    E, npe = m["nodes"].shape[:2]
+    f = I.poisson_source(m)
+    out = {"workload": "poisson2d_16x16_p3_C11_C22_0.05"}
+    eq = {"kind": "poisson", "C11": 0.05, "C22": 0.05, "C11b": 1.0, "bc": {0: "dirichlet"}, "source": f,
+          "gD": np.zeros_like(f)}
+    h = ldg.ldg_setup(m, eq)
+    U = torch.zeros((E, 1, npe), dtype=torch.float64, device="cuda")
+    Q = torch.zeros((E, 1, 2, npe), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ldg.ldg_coupled_solve(h, U, Q, rtol=1e-10, restart=64, max_cycles=100)
+    wall = time.perf_counter() - t0
+    out.update({"wall_ms_first_solve": wall * 1e3, "precond_build_ms": st["t_precond_ms"],
+                "gmres_ms": st["t_linear_ms"], "gmres_its": st["gmres_its"], "cycles": st["newton_its"],
+                "res_final_rel": st["res_final"] / st["res0"],
+                "err_u": float(np.abs(U.cpu().numpy() - I.poisson_exact(m)).max()),
+                "err_q": float(np.abs(Q.cpu().numpy() - I.poisson_exact_grad(m)).max())})
+    U.zero_()
+    Q.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ldg.ldg_coupled_solve(h, U, Q, rtol=1e-10, restart=64, max_cycles=100)
+    out["wall_ms_resolve"] = (time.perf_counter() - t0) * 1e3
+    G = torch.empty_like(Q)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out["gradient_uq_ms"] = _kernel_ms(torch, flush, lambda: ldg.ldg_gradient_uq(h, U, Q, G), 20)
+    eq0 = dict(eq, C11=0.0, C22=0.0)
+    h0 = ldg.ldg_setup(m, eq0)
+    U0 = torch.zeros_like(U)
+    ldg.ldg_steady_solve(h0, U0, 1.0, 1.0, 0, ldg.solver_opts(mode=ldg.MODE_FP64, rtol=1e-10, max_newton=30,
+                                                                 restart=64))
+    Q0 = torch.empty_like(Q)
+    ldg.ldg_gradient(h0, U0, Q0)
+    out["minimal_dissipation"] = {"err_u": float(np.abs(U0.cpu().numpy() - I.poisson_exact(m)).max()),
+                                  "err_q": float(np.abs(Q0.cpu().numpy() - I.poisson_exact_grad(m)).max())}
+    return out
+
+
 def learned_section(args):
     """The learned Newton guess on the Taylor-Green vortex at 16^3, p = 3:
     trajectories from the implicit solver for Re ~ U[400, 1600], GPU
@@ -676,6 +733,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess section")
     ap.add_argument("--no-channel", action="store_true", help="skip the 3-D walled channel section")
     ap.add_argument("--channel", type=int, nargs=3, default=[64, 32, 32])
+    ap.add_argument("--no-stabilized", action="store_true", help="skip the stabilised-LDG Poisson section")
     ap.add_argument("--channel-cfl", type=float, default=50.0)
     ap.add_argument("--learn-n", type=int, default=16)
     ap.add_argument("--learn-dt", type=float, default=0.03)

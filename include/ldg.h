@@ -105,6 +105,12 @@ typedef struct {
  *                     faces carries one vector for both. The flux does not
  *                     depend on the state, so its Jacobian entries are zero;
  *                     the gradient's trace there is the inside value.
+ *   C22               LDG penalty on the jump of the normal viscous flux in
+ *                     the trace u^ (Eq. 26; >= 0, Poisson only). 0 is the
+ *                     minimal-dissipation scheme every other call computes;
+ *                     with C22 > 0 the gradient depends on itself, and only
+ *                     ldg_gradient_uq, ldg_residual_uq and ldg_coupled_solve
+ *                     accept the handle (others return LDG_ERR_UNSUPPORTED).
  */
 typedef struct {
   int32_t kind;
@@ -120,6 +126,7 @@ typedef struct {
   const double* g_D;
   const double* source;
   const double* g_N;
+  double C22;
 } ldg_equations_t;
 
 typedef struct ldg_handle ldg_handle_t;
@@ -375,6 +382,47 @@ int ldg_rk4_step(ldg_handle_t* h, double* U_next, const double* U_n, double dt, 
  */
 int ldg_steady_solve(ldg_handle_t* h, double* U, double dt0, double growth, int32_t n_steps,
                      const ldg_solver_opts_t* opts, ldg_step_stats_t* stats, void* stream);
+
+/*
+ * The stabilised LDG scheme (C22 > 0 in ldg_equations_t; scalar Poisson,
+ * Sec. 3 Eqs. 25-26 and 30, Table 2's lower half). The trace u^ carries
+ * C22 (F.n(inside) - F.n(outside)) with F = -q and the unit normal (the sign
+ * that penalises the jump of the normal flux), so the gradient depends on
+ * itself and the steady problem is the coupled split system of Eq. 36,
+ *   Phi(U, Q) = (R(U, Q), Q - D(U, Q)) = 0.
+ *
+ * ldg_gradient_uq: Qout = D(U, Q) (also valid with C22 = 0, where Q may be
+ * NULL and the result is ldg_gradient's). U [n_elem][1][(p+1)^D], Q and Qout
+ * [n_elem][1][D][(p+1)^D], device FP64; Q and Qout may not alias.
+ * Errors: LDG_ERR_ARG (NULL U/Qout, Q NULL with C22 > 0, Q == Qout),
+ * LDG_ERR_UNSUPPORTED (first-order equations; Q with n_c > 1).
+ */
+int ldg_gradient_uq(ldg_handle_t* h, const double* U, const double* Q, double* Qout, void* stream);
+
+/*
+ * ldg_coupled_solve: solves Phi(U, Q) = 0 (Poisson, any C22 >= 0) by
+ * right-preconditioned restarted GMRES(restart) on its Jacobian
+ * [[K11, K12], [-K21, I - K22]] (Sec. 4.1), applied matrix-free by the
+ * gradient and residual kernels without boundary data and source. The
+ * preconditioner is the element block-Jacobi of that Jacobian (each
+ * element's U and Q rows against its own U and Q columns, couplings between
+ * elements dropped, as in Sec. 4.2), probed once per handle column by column
+ * on a colouring of the elements and inverted on the device; it needs
+ * (1 + D)(p+1)^D <= 128. Each cycle restarts from the true residual
+ * Phi(U, Q); the solve stops when ||Phi||_2 <= rtol ||Phi(U_in, Q_in)||_2.
+ * U, Q: device FP64, in: the initial guess (zeros are fine), out: the
+ * solution. stats: newton_its = GMRES cycles, gmres_its = iterations,
+ * res0 / res_final = ||Phi||_2 at entry / return, t_precond_ms = the
+ * preconditioner build (first call), t_linear_ms = the iterations. The
+ * handle keeps the preconditioner and the Krylov basis ((restart + 6) vectors
+ * of (1 + D) ndof doubles) until ldg_destroy. Synchronises on stream.
+ * Errors: LDG_ERR_ARG (rtol <= 0, restart outside 1..64, max_cycles < 1),
+ * LDG_ERR_UNSUPPORTED (not Poisson; block too large), LDG_ERR_NEWTON_MAXIT
+ * (target not met in max_cycles cycles; U, Q hold the last iterate),
+ * LDG_ERR_NONFINITE, LDG_ERR_GMRES_BREAKDOWN, LDG_ERR_CUDA.
+ */
+int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double rtol, int32_t restart, int32_t max_cycles,
+                      ldg_step_stats_t* stats, void* stream);
 
 /* ---- learned Newton predictor (not in the paper) ------------------------
  * A line-local MLP n_in -> 128 -> 128 -> 128 -> n_out with GELU (tanh form)

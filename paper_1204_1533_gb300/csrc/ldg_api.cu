@@ -68,8 +68,8 @@ cudaError_t smem_attr_cached(const void* fn, size_t bytes) {
 
 cudaError_t residual_2d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
 cudaError_t residual_3d(const ldg_handle* h, const double* U, const double* Q, double* R, cudaStream_t st);
-cudaError_t gradient_2d(const ldg_handle* h, const double* U, double* Q, cudaStream_t st);
-cudaError_t gradient_3d(const ldg_handle* h, const double* U, double* Q, cudaStream_t st);
+cudaError_t gradient_2d(const ldg_handle* h, const double* U, const double* Qs, double* Q, cudaStream_t st);
+cudaError_t gradient_3d(const ldg_handle* h, const double* U, const double* Qs, double* Q, cudaStream_t st);
 
 bool residual_supported(int D, int p, int kind) {
   if (p < 1 || p > 4) return false;
@@ -79,7 +79,12 @@ bool residual_supported(int D, int p, int kind) {
 }
 
 cudaError_t launch_gradient(const ldg_handle* h, const double* U, double* Q, cudaStream_t st) {
-  return h->D == 2 ? gradient_2d(h, U, Q, st) : gradient_3d(h, U, Q, st);
+  return h->D == 2 ? gradient_2d(h, U, nullptr, Q, st) : gradient_3d(h, U, nullptr, Q, st);
+}
+
+cudaError_t launch_gradient_uq(const ldg_handle* h, const double* U, const double* Qs, double* Q,
+                               cudaStream_t st) {
+  return h->D == 2 ? gradient_2d(h, U, Qs, Q, st) : gradient_3d(h, U, Qs, Q, st);
 }
 
 cudaError_t launch_residual(const ldg_handle* h, const double* U, const double* Q, double* R,
@@ -124,8 +129,14 @@ using namespace ldg;
 
 extern "C" int ldg_gradient(ldg_handle_t* h, const double* U, double* Q, void* stream) {
   if (!h || !U || !Q) return LDG_ERR_ARG;
-  if (!h->viscous()) return LDG_ERR_UNSUPPORTED;
+  if (!h->viscous() || h->phys.C22 != 0.0) return LDG_ERR_UNSUPPORTED;
   return launch_gradient(h, U, Q, (cudaStream_t)stream) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_gradient_uq(ldg_handle_t* h, const double* U, const double* Qs, double* Q, void* stream) {
+  if (!h || !U || !Q || (h->phys.C22 != 0.0 && !Qs) || (Qs && Qs == Q)) return LDG_ERR_ARG;
+  if (!h->viscous() || (Qs && h->nc != 1)) return LDG_ERR_UNSUPPORTED;
+  return launch_gradient_uq(h, U, Qs, Q, (cudaStream_t)stream) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
 }
 
 extern "C" int ldg_residual_uq(ldg_handle_t* h, const double* U, const double* Q, double* R,
@@ -136,6 +147,7 @@ extern "C" int ldg_residual_uq(ldg_handle_t* h, const double* U, const double* Q
 
 extern "C" int ldg_residual(ldg_handle_t* h, const double* U, double* R, void* stream) {
   if (!h || !U || !R) return LDG_ERR_ARG;
+  if (h->phys.C22 != 0.0) return LDG_ERR_UNSUPPORTED;  // D depends on Q: ldg_coupled_solve
   cudaStream_t st = (cudaStream_t)stream;
   if (h->viscous() && launch_gradient(h, U, h->Qbuf, st) != cudaSuccess) return LDG_ERR_CUDA;
   return launch_residual(h, U, h->viscous() ? h->Qbuf : nullptr, R, st) == cudaSuccess

@@ -58,6 +58,7 @@ struct Tab {
 
 struct PhysArgs {
   double gamma, mu, Pr, C11, C11b;
+  double C22;  // LDG flux-jump penalty (Poisson only; 0 = minimal dissipation)
   double adv[3];
   int flux;
   int nbc;
@@ -79,6 +80,10 @@ struct Geo {
 
 cudaError_t launch_gradient(const struct ::ldg_handle* h, const double* U, double* Q,
                             cudaStream_t st);
+// D(U, Qs) of the stabilised scheme (C22 != 0): the trace also takes the
+// jump of the normal flux of the given gradient Qs (Qs may not alias Q)
+cudaError_t launch_gradient_uq(const struct ::ldg_handle* h, const double* U, const double* Qs, double* Q,
+                               cudaStream_t st);
 cudaError_t launch_residual(const struct ::ldg_handle* h, const double* U, const double* Q,
                             double* R, cudaStream_t st);
 bool residual_supported(int D, int p, int kind);
@@ -120,6 +125,7 @@ struct ldg_handle {
   double* Qbuf = nullptr;    // LDG gradient of the last residual [E][nc][D][npe]
   double* dirk = nullptr;    // DIRK3 stage vectors K1..K3, B, U_i [5][ndof]
   double* red = nullptr;     // reduction scratch (doubles)
+  struct ldg_cpl* cpl = nullptr;  // coupled (U, Q) solver state of the stabilised scheme
   int64_t red_len = 0;
   ldg::Geo geo() const {
     ldg::Geo g;
@@ -178,6 +184,9 @@ cudaError_t launch_precond(const ldg_handle* h, const ldg_jac* J, double shift, 
 cudaError_t launch_precond_apply(const ldg_handle* h, const ldg_pc* P, const void* r, void* z,
                                  int vprec, cudaStream_t st);
 }  // namespace ldg
+
+// releases the coupled-solver state of a handle (ldg_solver.cu)
+void free_coupled(struct ldg_cpl* c);
 
 #define LDG_CUDA_TRY(x)                      \
   do {                                       \

@@ -25,6 +25,7 @@ namespace ldg {
 
 bool ops_supported(const ldg_handle* h) {
   if (h->p < 1 || h->p > 4) return false;
+  if (h->phys.C22 != 0.0) return false;  // coupled (U, Q) system: ldg_coupled_solve
   if (h->has_wall && h->kind != LDG_EQ_EULER && h->kind != LDG_EQ_NAVIER_STOKES) return false;
   if (h->D == 2) return true;
   return h->kind == LDG_EQ_EULER || h->kind == LDG_EQ_NAVIER_STOKES;

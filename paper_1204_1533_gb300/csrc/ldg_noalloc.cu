@@ -44,6 +44,7 @@ int scratch_address(double** out) {
 
 extern "C" int ldg_residual_noalloc(ldg_handle_t* h, const double* U, double* R, void* stream) {
   if (!h || !U || !R) return LDG_ERR_ARG;
+  if (h->phys.C22 != 0.0) return LDG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   if (!h->viscous())  // first-order equations need no scratch
     return ldg::launch_residual(h, U, nullptr, R, st) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;

@@ -8,7 +8,7 @@ namespace ldg {
     return run_residual<3, P, EQ>(h, U, Q, R, st);
 #define LDG_GRAD_CASE(NC, P) \
   case P:                    \
-    return run_gradient<3, P, NC>(h, U, Q, st);
+    return run_gradient<3, P, NC>(h, U, Qs, Q, st);
 
 cudaError_t residual_3d(const ldg_handle* h, const double* U, const double* Q, double* R,
                         cudaStream_t st) {
@@ -29,7 +29,7 @@ cudaError_t residual_3d(const ldg_handle* h, const double* U, const double* Q, d
   return cudaErrorInvalidValue;
 }
 
-cudaError_t gradient_3d(const ldg_handle* h, const double* U, double* Q, cudaStream_t st) {
+cudaError_t gradient_3d(const ldg_handle* h, const double* U, const double* Qs, double* Q, cudaStream_t st) {
   if (h->nc == 1) {
     switch (h->p) { LDG_GRAD_CASE(1, 1) LDG_GRAD_CASE(1, 2) LDG_GRAD_CASE(1, 3) LDG_GRAD_CASE(1, 4) }
   } else if (h->nc == 5) {

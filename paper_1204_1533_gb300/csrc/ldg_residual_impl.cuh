@@ -44,10 +44,14 @@ struct Shape {
 
 // ---------------------------------------------------------------------------
 // Q = D(U): per line d^(d)_i = L1_i u^+ n^+ + L0_i u^- n^- - sum_q Kd_iq u(xi_q) n_d(xi_q)
+// With Qs (scalar Poisson, C22 != 0) the trace at interior ends adds
+// C22 (F.n^(in) - F.n^(out)) with F = -q and the unit normal, and at Neumann
+// ends C22 (F.n^(in) - G.n): D(U, Q) of the stabilised scheme (Eqs. 26, 30).
 // ---------------------------------------------------------------------------
 template <int D, int P, int NC>
 __global__ void __launch_bounds__(Shape<D, P>::THREADS)
-    k_gradient(const double* __restrict__ U, double* __restrict__ Q, Geo g, Tab tab, PhysArgs ph) {
+    k_gradient(const double* __restrict__ U, const double* __restrict__ Qs, double* __restrict__ Q, Geo g,
+               Tab tab, PhysArgs ph) {
   using S = Shape<D, P>;
   constexpr int N = S::N, NPE = S::NPE, NQ = S::NQ;
   constexpr int tile = NC * NPE;
@@ -74,7 +78,8 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
     for (int end = 0; end < 2; ++end)
 #pragma unroll
       for (int a = 0; a < D; ++a) nv[end][a] = g.nend[(L * 2 + end) * D + a];
-    // trace u^ at both ends (Eq. 26 with C22 = 0; Eq. 28 at Dirichlet faces)
+    // trace u^ at both ends (Eq. 26; Eq. 28 at Dirichlet faces, Eq. 30 at
+    // Neumann faces)
     double uh[2][NC];
 #pragma unroll
     for (int end = 0; end < 2; ++end) {
@@ -83,21 +88,46 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
       double uin[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) uin[c] = uel[c * NPE + aend];
+      // stabilised scheme: unit-normal flux F.n/|n| = -q.n/|n| of the inside trace
+      double fin = 0.0, nrm = 1.0;
+      const bool stab = NC == 1 && Qs != nullptr;
+      if (stab) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s += nv[end][a] * nv[end][a];
+        nrm = sqrt(s);
+#pragma unroll
+        for (int a = 0; a < D; ++a) fin -= Qs[(e * D + a) * NPE + aend] * nv[end][a];
+        fin /= nrm;
+      }
       if (nb >= 0) {
+        const int64_t eo = nb / NPE;
+        const int ao = nb % NPE;
         if (g.sw[(e * D + d) * 2 + end] == 1) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) uh[end][c] = uin[c];
         } else {
-          const int64_t eo = nb / NPE;
-          const int ao = nb % NPE;
 #pragma unroll
           for (int c = 0; c < NC; ++c) uh[end][c] = U[eo * tile + c * NPE + ao];
         }
+        if (stab) {
+          double fout = 0.0;
+#pragma unroll
+          for (int a = 0; a < D; ++a) fout -= Qs[(eo * D + a) * NPE + ao] * nv[end][a];
+          uh[end][0] += ph.C22 * (fin - fout / nrm);
+        }
       } else {
         const int kind = ph.bck[-1 - nb];
-        if (kind == BC_NEUMANN) {  // Eq. 30 with C22 = 0
+        if (kind == BC_NEUMANN) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) uh[end][c] = uin[c];
+          if (stab) {
+            double gn = 0.0;
+            if (g.gN)
+#pragma unroll
+              for (int a = 0; a < D; ++a) gn += g.gN[(e * D + a) * NPE + aend] * nv[end][a];
+            uh[end][0] += ph.C22 * (fin - gn / nrm);
+          }
           continue;
         }
         if constexpr (NC == D + 2) {
@@ -349,14 +379,14 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
 }
 
 template <int D, int P, int NC>
-cudaError_t run_gradient(const ldg_handle* h, const double* U, double* Q, cudaStream_t st) {
+cudaError_t run_gradient(const ldg_handle* h, const double* U, const double* Qs, double* Q, cudaStream_t st) {
   using S = Shape<D, P>;
   const size_t smem = (size_t)S::EPB * (NC * S::NPE + D * NC * D * S::NPE) * sizeof(double);
   auto kern = k_gradient<D, P, NC>;
   cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
-  kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, h->geo(), h->tab, h->phys);
+  kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Qs, Q, h->geo(), h->tab, h->phys);
   count_launch();
   return cudaGetLastError();
 }

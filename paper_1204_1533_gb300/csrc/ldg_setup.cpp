@@ -219,6 +219,8 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
   if (!mesh->s || !mesh->nodes || !mesh->vertices || !mesh->btag) return LDG_ERR_ARG;
   if (eq->kind < 0 || eq->kind > 3) return LDG_ERR_ARG;
   if (eq->n_bc < 0 || eq->n_bc > ldg::MAXBC) return LDG_ERR_ARG;
+  if (!(eq->C22 >= 0.0)) return LDG_ERR_ARG;
+  if (eq->C22 != 0.0 && eq->kind != LDG_EQ_POISSON) return LDG_ERR_UNSUPPORTED;
   for (int t = 0; t < eq->n_bc && eq->bc_kind; ++t)
     if (eq->bc_kind[t] < LDG_BC_DIRICHLET || eq->bc_kind[t] > LDG_BC_NEUMANN) return LDG_ERR_ARG;
   if (!ldg::residual_supported(D, p, eq->kind)) return LDG_ERR_UNSUPPORTED;
@@ -246,6 +248,7 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
   h->phys.Pr = eq->Pr;
   h->phys.C11 = eq->C11;
   h->phys.C11b = eq->C11_b;
+  h->phys.C22 = eq->C22;
   for (int a = 0; a < 3; ++a) h->phys.adv[a] = eq->adv[a];
   h->phys.flux = eq->flux;
   h->phys.nbc = eq->n_bc;
@@ -653,6 +656,7 @@ extern "C" int ldg_destroy(ldg_handle_t* h) {
   cudaFree(h->invJ);
   cudaFree(h->gD);
   cudaFree(h->gN);
+  free_coupled(h->cpl);
   cudaFree(h->src);
   cudaFree(h->Qbuf);
   cudaFree(h->dirk);

@@ -769,3 +769,320 @@ extern "C" int ldg_set_viscosity(ldg_handle_t* h, double mu) {
   h->jac_age = 1 << 30;  // the retained Jacobian belongs to the old viscosity
   return LDG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Stabilised LDG (C22 > 0, scalar Poisson): the coupled split system of
+// Eq. 36, Phi(U, Q) = (R(U, Q), Q - D(U, Q)) = 0, which is affine in (U, Q).
+// Right-preconditioned restarted GMRES(m) on its Jacobian J = [[K11, K12],
+// [-K21, I - K22]] applied matrix-free by the residual and gradient kernels
+// with the boundary data and source switched off (J x = Phi_0(x), exact for
+// the affine map). Preconditioner: element block-Jacobi of J, the element's
+// U and Q rows against its own U and Q columns (all couplings between
+// elements dropped, as in Sec. 4.2), probed column by column with unit
+// vectors on a colouring of the elements in which face neighbours differ,
+// then inverted by Gauss-Jordan with partial pivoting, one block per element.
+// ---------------------------------------------------------------------------
+struct ldg_cpl {
+  int B = 0, ncolors = 0, m = 0;
+  int64_t M = 0;
+  bool built = false;
+  int32_t* color = nullptr;  // [E]
+  double* Binv = nullptr;    // [E][B][B]
+  double* buf = nullptr;     // vectors and Krylov basis
+  double *x, *r, *phi, *z, *t, *Vb, *Gt, *part, *hcol, *hacc, *y;
+};
+
+void free_coupled(ldg_cpl* c) {
+  if (!c) return;
+  cudaFree(c->color);
+  cudaFree(c->Binv);
+  cudaFree(c->buf);
+  delete c;
+}
+
+namespace ldg {
+
+// local row/column k of element e in the coupled vector [U (N) | Q (N D)]
+__device__ __forceinline__ int64_t cpl_index(int64_t e, int k, int npe, int D, int64_t N) {
+  return k < npe ? e * npe + k : N + e * (int64_t)D * npe + (k - npe);
+}
+
+__global__ void k_cpl_probe(double* __restrict__ v, const int32_t* __restrict__ color, int c, int k, int64_t E,
+                            int npe, int D, int64_t N) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E && color[e] == c) v[cpl_index(e, k, npe, D, N)] = 1.0;
+}
+
+// A[e][r][k] = y[row r of element e] for the elements of colour c
+__global__ void k_cpl_gather(double* __restrict__ A, const double* __restrict__ y, const int32_t* __restrict__ color,
+                             int c, int k, int B, int64_t E, int npe, int D, int64_t N) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * B) return;
+  const int64_t e = t / B;
+  const int r = (int)(t % B);
+  if (color[e] != c) return;
+  A[(e * B + r) * B + k] = y[cpl_index(e, r, npe, D, N)];
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting of each B x B block
+// (B <= 128), one block of threads per element; the row permutation is
+// undone on the columns at the end. A singular pivot leaves NaN.
+__global__ void __launch_bounds__(128) k_cpl_invert(double* __restrict__ A, int B) {
+  double* a = A + (int64_t)blockIdx.x * B * B;
+  __shared__ double f[128];
+  __shared__ int piv[128];
+  __shared__ int prow;
+  for (int c = 0; c < B; ++c) {
+    if (threadIdx.x == 0) {
+      int best = c;
+      double bv = fabs(a[c * B + c]);
+      for (int r = c + 1; r < B; ++r)
+        if (fabs(a[r * B + c]) > bv) {
+          bv = fabs(a[r * B + c]);
+          best = r;
+        }
+      prow = best;
+      piv[c] = best;
+    }
+    __syncthreads();
+    const int pr = prow;
+    if (pr != c)
+      for (int j = threadIdx.x; j < B; j += blockDim.x) {
+        const double tmp = a[c * B + j];
+        a[c * B + j] = a[pr * B + j];
+        a[pr * B + j] = tmp;
+      }
+    __syncthreads();
+    const double d = 1.0 / a[c * B + c];
+    for (int r = threadIdx.x; r < B; r += blockDim.x) f[r] = a[r * B + c];
+    __syncthreads();
+    // row c: scaled, with the inverse's column c in place of the pivot column
+    for (int j = threadIdx.x; j < B; j += blockDim.x) a[c * B + j] = (j == c ? 1.0 : a[c * B + j]) * d;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < B * B; idx += blockDim.x) {
+      const int r = idx / B, j = idx % B;
+      if (r == c) continue;
+      const double arj = (j == c) ? 0.0 : a[r * B + j];
+      a[r * B + j] = arj - f[r] * a[c * B + j];
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int c = B - 1; c >= 0; --c) {
+    const int pr = piv[c];
+    if (pr != c)
+      for (int r = threadIdx.x; r < B; r += blockDim.x) {
+        const double tmp = a[r * B + c];
+        a[r * B + c] = a[r * B + pr];
+        a[r * B + pr] = tmp;
+      }
+    __syncthreads();
+  }
+}
+
+// z_e = Binv_e v_e, one block of threads per element, one thread per row
+__global__ void __launch_bounds__(128) k_cpl_apply(double* __restrict__ z, const double* __restrict__ v,
+                                                   const double* __restrict__ Binv, int B, int npe, int D,
+                                                   int64_t N) {
+  const int64_t e = blockIdx.x;
+  __shared__ double ve[128];
+  for (int k = threadIdx.x; k < B; k += blockDim.x) ve[k] = v[cpl_index(e, k, npe, D, N)];
+  __syncthreads();
+  const double* a = Binv + e * B * B;
+  for (int r = threadIdx.x; r < B; r += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < B; ++k) s = fma(a[r * B + k], ve[k], s);
+    z[cpl_index(e, r, npe, D, N)] = s;
+  }
+}
+
+// y = q - g
+__global__ void k_sub(double* __restrict__ y, const double* __restrict__ q, const double* __restrict__ g, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = q[i] - g[i];
+}
+
+// out = Phi(x) of handle hh (the full map, or its linear part when hh carries
+// no boundary data and no source); Gt: gradient scratch [N D]
+static int cpl_phi(const ldg_handle* hh, const double* x, double* out, double* Gt, cudaStream_t st) {
+  const int64_t N = hh->ndof, NQ = N * hh->D;
+  if (launch_gradient_uq(hh, x, x + N, Gt, st) != cudaSuccess) return LDG_ERR_CUDA;
+  if (launch_residual(hh, x, x + N, out, st) != cudaSuccess) return LDG_ERR_CUDA;
+  k_sub<<<grid_for(NQ), 256, 0, st>>>(out + N, x + N, Gt, NQ);
+  count_launch();
+  LDG_CUDA_TRY(cudaGetLastError());
+  return LDG_OK;
+}
+
+}  // namespace ldg
+
+extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double rtol, int32_t restart,
+                                 int32_t max_cycles, ldg_step_stats_t* stats, void* stream) {
+  if (!h || !U || !Q || !stats || !(rtol > 0) || restart < 1 || restart > 64 || max_cycles < 1)
+    return LDG_ERR_ARG;
+  if (h->kind != LDG_EQ_POISSON || h->nc != 1) return LDG_ERR_UNSUPPORTED;
+  const int npe = h->npe, D = h->D, B = npe * (1 + D), m = restart;
+  if (B > 128) return LDG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t E = h->E, N = h->ndof, M = N * (1 + D);
+  *stats = ldg_step_stats_t{};
+  // the linear part of Phi: the same handle without boundary data and source
+  ldg_handle hh = *h;
+  hh.gD = nullptr;
+  hh.gN = nullptr;
+  hh.src = nullptr;
+  ldg_cpl* c = h->cpl;
+  if (c && c->m < m) {  // grow the Krylov basis
+    free_coupled(c);
+    c = h->cpl = nullptr;
+  }
+  if (!c) {
+    c = new ldg_cpl();
+    h->cpl = c;
+    c->B = B;
+    c->M = M;
+    c->m = m;
+    // colouring: face neighbours (every outside node of every line end) differ
+    std::vector<int32_t> col(E, -1);
+    std::vector<char> used;
+    for (int64_t e = 0; e < E; ++e) {
+      used.assign(64, 0);
+      for (int64_t k = e * D * h->nl * 2; k < (e + 1) * D * h->nl * 2; ++k) {
+        const int32_t nb = h->nbr_h[k];
+        if (nb < 0) continue;
+        const int64_t eo = nb / npe;
+        if (eo != e && col[eo] >= 0 && col[eo] < 64) used[col[eo]] = 1;
+      }
+      int cc = 0;
+      while (cc < 64 && used[cc]) ++cc;
+      if (cc == 64) return LDG_ERR_MESH;
+      col[e] = cc;
+      if (cc + 1 > c->ncolors) c->ncolors = cc + 1;
+    }
+    const size_t parts = (size_t)(m + 2) * MDOT_BLOCKS > (size_t)OKMAX * ORTHO_BLOCKS
+                             ? (size_t)(m + 2) * MDOT_BLOCKS
+                             : (size_t)OKMAX * ORTHO_BLOCKS;
+    const size_t nbuf = (size_t)M * (5 + m + 1) + (size_t)N * D + parts + 3 * (size_t)(m + 2);
+    LDG_CUDA_TRY(cudaMalloc((void**)&c->color, E * sizeof(int32_t)));
+    LDG_CUDA_TRY(cudaMalloc((void**)&c->Binv, (size_t)E * B * B * sizeof(double)));
+    LDG_CUDA_TRY(cudaMalloc((void**)&c->buf, nbuf * sizeof(double)));
+    LDG_CUDA_TRY(cudaMemcpyAsync(c->color, col.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    double* p = c->buf;
+    c->x = p; p += M;
+    c->r = p; p += M;
+    c->phi = p; p += M;
+    c->z = p; p += M;
+    c->t = p; p += M;
+    c->Vb = p; p += (size_t)M * (m + 1);
+    c->Gt = p; p += (size_t)N * D;
+    c->part = p; p += parts;
+    c->hcol = p; p += m + 2;
+    c->hacc = p; p += m + 2;
+    c->y = p;
+    LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  int rc;
+  if (!c->built) {  // probe the element blocks of J and invert them
+    PhaseTimer tp(st, &stats->t_precond_ms);
+    for (int cc = 0; cc < c->ncolors; ++cc)
+      for (int k = 0; k < B; ++k) {
+        LDG_CUDA_TRY(cudaMemsetAsync(c->z, 0, M * sizeof(double), st));
+        k_cpl_probe<<<(unsigned)((E + 255) / 256), 256, 0, st>>>(c->z, c->color, cc, k, E, npe, D, N);
+        count_launch();
+        if ((rc = cpl_phi(&hh, c->z, c->t, c->Gt, st))) return rc;
+        k_cpl_gather<<<(unsigned)((E * B + 255) / 256), 256, 0, st>>>(c->Binv, c->t, c->color, cc, k, B, E, npe,
+                                                                       D, N);
+        count_launch();
+      }
+    k_cpl_invert<<<(unsigned)E, 128, 0, st>>>(c->Binv, B);
+    count_launch();
+    LDG_CUDA_TRY(cudaGetLastError());
+    c->built = true;
+  }
+  Work w{};
+  w.part = c->part;
+  w.hcol = c->hcol;
+  w.hacc = c->hacc;
+  w.y = c->y;
+  auto nrm = [&](const double* v, double* out) -> int {
+    if (mdot<double>(v, 1, M, v, c->part, c->hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
+    double s = 0;
+    LDG_CUDA_TRY(cudaMemcpyAsync(&s, c->hcol, 8, cudaMemcpyDeviceToHost, st));
+    LDG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!std::isfinite(s)) return LDG_ERR_NONFINITE;
+    *out = std::sqrt(s);
+    return LDG_OK;
+  };
+  PhaseTimer tl(st, &stats->t_linear_ms);
+  // x = (U, Q); r = -Phi(x)
+  LDG_CUDA_TRY(cudaMemcpyAsync(c->x, U, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  LDG_CUDA_TRY(cudaMemcpyAsync(c->x + N, Q, N * D * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double res0 = 0, res = 0;
+  if ((rc = cpl_phi(h, c->x, c->phi, c->Gt, st))) return rc;
+  if ((rc = nrm(c->phi, &res0))) return rc;
+  stats->res0 = res = res0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hc(m + 2);
+  for (int cyc = 0; cyc < max_cycles && res > rtol * res0; ++cyc) {
+    stats->newton_its += 1;
+    // V_0 = -Phi(x) / ||Phi(x)||
+    k_scale_to<double, double><<<grid_for(M), 256, 0, st>>>(c->Vb, c->phi, -1.0 / res, M);
+    count_launch();
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = res;
+    int k_used = 0;
+    for (int k = 0; k < m; ++k) {
+      double* vk = c->Vb + (int64_t)k * M;
+      double* vn = c->Vb + (int64_t)(k + 1) * M;
+      k_cpl_apply<<<(unsigned)E, 128, 0, st>>>(c->z, vk, c->Binv, B, npe, D, N);
+      count_launch();
+      if ((rc = cpl_phi(&hh, c->z, vn, c->Gt, st))) return rc;
+      LDG_CUDA_TRY(cudaMemsetAsync(c->hacc, 0, (k + 2) * sizeof(double), st));
+      if (cgs2<double>(c->Vb, k + 1, M, vn, w, st) != cudaSuccess) return LDG_ERR_CUDA;
+      LDG_CUDA_TRY(cudaMemcpyAsync(hc.data(), c->hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      LDG_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
+      const double hn = std::sqrt(hc[k + 1]);
+      if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
+      if (hn > 0) {
+        k_scale_to<double, double><<<grid_for(M), 256, 0, st>>>(vn, vn, 1.0 / hn, M);
+        count_launch();
+      }
+      for (int j = 0; j < k; ++j) {
+        const double a = H[(size_t)j * m + k], b = H[(size_t)(j + 1) * m + k];
+        H[(size_t)j * m + k] = cs[j] * a + sn[j] * b;
+        H[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * b;
+      }
+      const double a = H[(size_t)k * m + k];
+      const double den = std::hypot(a, hn);
+      if (den == 0.0) return LDG_ERR_GMRES_BREAKDOWN;
+      cs[k] = a / den;
+      sn[k] = hn / den;
+      H[(size_t)k * m + k] = den;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      k_used = k + 1;
+      stats->gmres_its += 1;
+      if (std::fabs(g[k + 1]) <= rtol * res0 || hn == 0.0) break;
+    }
+    std::vector<double> yv(k_used);
+    for (int i = k_used - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int j = i + 1; j < k_used; ++j) s -= H[(size_t)i * m + j] * yv[j];
+      yv[i] = s / H[(size_t)i * m + i];
+    }
+    LDG_CUDA_TRY(cudaMemcpyAsync(c->y, yv.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_combine<double><<<grid_for(M), 256, 0, st>>>(c->t, c->Vb, c->y, k_used, M);
+    k_cpl_apply<<<(unsigned)E, 128, 0, st>>>(c->z, c->t, c->Binv, B, npe, D, N);
+    k_axpy_d<double><<<grid_for(M), 256, 0, st>>>(c->x, c->z, 1.0, M);
+    count_launch(3);
+    // the true residual of the affine map at the new iterate
+    if ((rc = cpl_phi(h, c->x, c->phi, c->Gt, st))) return rc;
+    if ((rc = nrm(c->phi, &res))) return rc;
+  }
+  stats->res_final = res;
+  LDG_CUDA_TRY(cudaMemcpyAsync(U, c->x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  LDG_CUDA_TRY(cudaMemcpyAsync(Q, c->x + N, N * D * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  return res <= rtol * res0 ? LDG_OK : LDG_ERR_NEWTON_MAXIT;
+}

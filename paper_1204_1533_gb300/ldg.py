@@ -43,7 +43,7 @@ class ldg_equations_t(C.Structure):
                 ("mu", C.c_double), ("Pr", C.c_double), ("C11", C.c_double),
                 ("C11_b", C.c_double), ("adv", C.c_double * 3), ("n_bc", C.c_int32),
                 ("bc_kind", C.c_void_p), ("g_D", C.c_void_p), ("source", C.c_void_p),
-                ("g_N", C.c_void_p)]
+                ("g_N", C.c_void_p), ("C22", C.c_double)]
 
 
 class ldg_solver_opts_t(C.Structure):
@@ -107,6 +107,8 @@ _SIGS = {
     "ldg_rk4_step": [_P, _P, _P, C.c_double, _P],
     "ldg_steady_solve": [_P, _P, C.c_double, C.c_double, C.c_int32, C.POINTER(ldg_solver_opts_t),
                          C.POINTER(ldg_step_stats_t), _P],
+    "ldg_gradient_uq": [_P, _P, _P, _P, _P],
+    "ldg_coupled_solve": [_P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.POINTER(ldg_step_stats_t), _P],
 }
 
 
@@ -199,7 +201,7 @@ class _Marshal:
             float(eq.get("C11b", 1.0)), (C.c_double * 3)(*adv[:3]), nbc, self.bck.ctypes.data,
             None if self.gD is None else self.gD.ctypes.data,
             None if self.src is None else self.src.ctypes.data,
-            None if self.gN is None else self.gN.ctypes.data)
+            None if self.gN is None else self.gN.ctypes.data, float(eq.get("C22", 0.0)))
 
 
 def ldg_setup_host(mesh, eq):
@@ -280,6 +282,20 @@ def ldg_residual(h, U, R, stream=None):
 def ldg_gradient(h, U, Q, stream=None):
     _check(lib().ldg_gradient(h.ptr, _dptr(U), _dptr(Q), _stream(stream)), "ldg_gradient")
     return Q
+
+
+def ldg_gradient_uq(h, U, Q, Qout, stream=None):
+    """D(U, Q) of the stabilised scheme (Q may be None when C22 = 0)."""
+    _check(lib().ldg_gradient_uq(h.ptr, _dptr(U), _dptr(Q), _dptr(Qout), _stream(stream)), "ldg_gradient_uq")
+    return Qout
+
+
+def ldg_coupled_solve(h, U, Q, rtol=1e-10, restart=64, max_cycles=200, stream=None):
+    """Solve (R(U, Q), Q - D(U, Q)) = 0 in place (Poisson, stabilised scheme)."""
+    st = ldg_step_stats_t()
+    _check(lib().ldg_coupled_solve(h.ptr, _dptr(U), _dptr(Q), float(rtol), int(restart), int(max_cycles),
+                                   C.byref(st), _stream(stream)), "ldg_coupled_solve")
+    return st.as_dict()
 
 
 def ldg_residual_uq(h, U, Q, R, stream=None):

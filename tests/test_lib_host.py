@@ -83,3 +83,14 @@ def test_rejects_bad_meshes():
     with pytest.raises(ldg.LdgError) as e:
         ldg.ldg_setup_host(I.vortex_mesh(3, 6), EULER)   # p not compiled in
     assert e.value.code == -8
+
+
+def test_stabilised_scheme_is_poisson_only():
+    m = I.poisson_square_mesh(3, 2)
+    ldg.ldg_setup_host(m, {"kind": "poisson", "C22": 0.05, "bc": {0: "dirichlet"}})
+    with pytest.raises(ldg.LdgError) as e:
+        ldg.ldg_setup_host(m, {"kind": "poisson", "C22": -0.05, "bc": {0: "dirichlet"}})
+    assert e.value.code == -1
+    with pytest.raises(ldg.LdgError) as e:
+        ldg.ldg_setup_host(I.vortex_mesh(3, 2), dict(EULER, C22=0.05))
+    assert e.value.code == -8
