@@ -75,6 +75,12 @@ extern "C" {
  *   btag     [n_elem][2D]             face f = 2d + end (end 0: X_d = 0, end 1:
  *                                     X_d = 1); -1 = interior (matched through
  *                                     vertex ids), >= 0 = boundary tag
+ *   switches [n_elem][D][2] or NULL  the switch function S^-_d, S^+_d (Sec. 3)
+ *                                     to use instead of deriving it: one part of a
+ *                                     partitioned mesh passes the global function
+ *                                     restricted to its elements. Checked: values
+ *                                     +-1, S^- = -S^+, opposite signs across
+ *                                     every matched face (else LDG_ERR_MESH)
  */
 typedef struct {
   int32_t D;
@@ -84,6 +90,7 @@ typedef struct {
   const double* nodes;
   const int64_t* vertices;
   const int32_t* btag;
+  const int8_t* switches;
 } ldg_mesh_t;
 
 /*

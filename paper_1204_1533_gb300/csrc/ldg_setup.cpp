@@ -406,6 +406,26 @@ static int host_setup(const ldg_mesh_t* mesh, const ldg_equations_t* eq, ldg_han
         }
       }
     }
+  if (mesh->switches) {  // the caller's switch function (a part of a partitioned mesh)
+    for (int64_t k = 0; k < E * D; ++k) {
+      const int8_t sm = mesh->switches[2 * k], sp = mesh->switches[2 * k + 1];
+      if ((sp != 1 && sp != -1) || sm != -sp) {
+        delete h;
+        return LDG_ERR_MESH;
+      }
+    }
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 2 * D; ++f) {
+        const int64_t en = nb_e[e * 2 * D + f];
+        if (en < 0) continue;
+        const int fn = nb_f[e * 2 * D + f];
+        if (mesh->switches[(e * D + f / 2) * 2 + f % 2] != -mesh->switches[(en * D + fn / 2) * 2 + fn % 2]) {
+          delete h;
+          return LDG_ERR_MESH;
+        }
+      }
+    std::memcpy(h->sw_h.data(), mesh->switches, h->sw_h.size());
+  }
   // ---- metric terms ------------------------------------------------------------
   linemet.assign((size_t)E * nl * D * D, 0.0f);
   ng.assign((size_t)E * D * nl * nq * D, 0.0);

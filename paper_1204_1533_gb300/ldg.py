@@ -35,7 +35,7 @@ class LdgError(RuntimeError):
 class ldg_mesh_t(C.Structure):
     _fields_ = [("D", C.c_int32), ("p", C.c_int32), ("n_elem", C.c_int64),
                 ("s", C.c_void_p), ("nodes", C.c_void_p), ("vertices", C.c_void_p),
-                ("btag", C.c_void_p)]
+                ("btag", C.c_void_p), ("switches", C.c_void_p)]
 
 
 class ldg_equations_t(C.Structure):
@@ -178,9 +178,12 @@ class _Marshal:
         self.nodes = np.ascontiguousarray(mesh["nodes"], dtype=np.float64)
         self.verts = np.ascontiguousarray(mesh["vertices"], dtype=np.int64)
         self.btag = np.ascontiguousarray(mesh["btag"], dtype=np.int32)
+        self.sw = None if mesh.get("switches") is None else np.ascontiguousarray(mesh["switches"], dtype=np.int8)
+        if self.sw is not None and self.sw.size != self.nodes.shape[0] * int(mesh["D"]) * 2:
+            raise ValueError("switches: expected [n_elem, D, 2]")
         self.mesh = ldg_mesh_t(int(mesh["D"]), int(mesh["p"]), int(self.nodes.shape[0]),
                                self.s.ctypes.data, self.nodes.ctypes.data, self.verts.ctypes.data,
-                               self.btag.ctypes.data)
+                               self.btag.ctypes.data, None if self.sw is None else self.sw.ctypes.data)
         bc = eq.get("bc", {0: "dirichlet"})
         nbc = (max(bc) + 1) if bc else 0
         self.bck = np.zeros(max(nbc, 1), dtype=np.int32)
