@@ -646,9 +646,11 @@ def stabilized_section(args):
     U.zero_()
     Q.zero_()
     torch.cuda.synchronize()
+    _nvtx(torch, "stabilized_resolve")
     t0 = time.perf_counter()
     st = ldg.ldg_coupled_solve(h, U, Q, rtol=1e-10, restart=64, max_cycles=100)
     out["wall_ms_resolve"] = (time.perf_counter() - t0) * 1e3
+    _nvtx(torch, None)
     G = torch.empty_like(Q)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out["gradient_uq_ms"] = _kernel_ms(torch, flush, lambda: ldg.ldg_gradient_uq(h, U, Q, G), 20)
