@@ -242,3 +242,33 @@ def test_rk4_fourth_order_on_dg_advection():
     e1 = np.abs(run(32) - ref).max()
     e2 = np.abs(run(64) - ref).max()
     assert 3.7 < math.log2(e1 / e2) < 4.4, (e1, e2)
+
+
+def test_bdf2_second_order_on_dg_advection():
+    """The BDF2 Newton driver (a BDF1 first level, then BDF2) on the DG
+    advection semi-discretisation, against the exact flow of that linear ODE
+    system (matrix exponential of its dense Jacobian): halving dt divides
+    the error by about 4 (the BDF1 start contributes O(dt^2) once)."""
+    import scipy.linalg as sla
+    m = I.structured_mesh((3, 3), 2, (0, 0), (1, 1), (True, True), perturb=0.1)
+    disc = Discretization(m, {"kind": "advection", "adv": [1.0, 0.6]})
+    x, y = m["nodes"][..., 0], m["nodes"][..., 1]
+    U0 = np.sin(2 * math.pi * x + 0.3)[:, None] * np.cos(2 * math.pi * y)[:, None]
+    F = lambda X: full_residual(disc, X)
+    K = JAC.K11(disc, U0)
+    jac = lambda X: (K, None, None)
+    T = 0.2
+    exact = (sla.expm(T * K.toarray()) @ U0.ravel()).reshape(U0.shape)
+
+    def run(nsteps):
+        dt = T / nsteps
+        Unm1, Un = None, U0.copy()
+        for k in range(nsteps):
+            U1, st = S.newton_bdf2(F, jac, Un, Unm1, dt, first=(k == 0), rtol=1e-13, gmres_tol=1e-14,
+                                   restart=200, reuse=100)
+            assert st["newton"] <= 2
+            Unm1, Un = Un, U1
+        return Un
+    e1 = np.abs(run(20) - exact).max()
+    e2 = np.abs(run(40) - exact).max()
+    assert 1.8 < math.log2(e1 / e2) < 2.3, (e1, e2)
