@@ -616,7 +616,7 @@ def channel_section(args, hbm):
 
 def stabilized_section(args):
     """The stabilised LDG scheme (C11 = C22 = 1/20) of Table 2's lower half on
-    configuration 1's finest mesh (16 x 16 perturbed quads, p = 3): the
+    the 16 x 16 perturbed unit square with p = 3 (the Poisson workload's finest mesh): the
     coupled (U, Q) solve with its element block-Jacobi preconditioner, the
     D(U, Q) kernel, and the errors against the manufactured solution next to
     the minimal-dissipation solve of the same mesh."""

@@ -409,7 +409,7 @@ def unstructured_hex_mesh(n=3, p=2, L=1.0, periodic=False, perturb=0.0, seed=MES
 
 
 # ---------------------------------------------------------------------------
-# workload meshes (sizes and perturbations of the benchmark configurations)
+# workload meshes (sizes and perturbations of the benchmark workloads)
 # ---------------------------------------------------------------------------
 def poisson_square_mesh(n=8, p=3, perturb=0.15, seed=MESH_SEED):
     """Unit square, n x n straight-sided quads, interior vertices perturbed by

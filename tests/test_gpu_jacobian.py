@@ -404,7 +404,7 @@ def test_rk4_vortex_convergence_on_gpu(L):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_poisson_steady_solve_and_rates(L, mode):
-    """Configuration 1 on the GPU: -lap u = f on the perturbed unit square,
+    """The Poisson workload on the GPU: -lap u = f on the perturbed unit square,
     p = 3, solved by the steady driver (one step without the time
     derivative); the solution matches the oracle's direct solve, and the
     error falls at the rate of the paper's Table 2 (p + 1)."""

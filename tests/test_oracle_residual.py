@@ -234,7 +234,7 @@ def test_euler_vortex_truncation_converges():
 
 
 # ---------------------------------------------------------------------------
-# Poisson (LDG, configuration 1)
+# Poisson (LDG, the perturbed unit square)
 # ---------------------------------------------------------------------------
 POISSON = {"kind": "poisson", "C11b": 1.0, "bc": {0: "dirichlet"}}
 
