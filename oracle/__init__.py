@@ -17,10 +17,13 @@ Modules and what each follows:
              (Sec. 2.1 Eqs. 2, 4-6; Sec. 2.2; Sec. 3 switch construction)
   physics    Euler/Navier-Stokes/Poisson/advection fluxes, Roe and
              Lax-Friedrichs numerical fluxes (Sec. 5.2 Eqs. 44-48, Sec. 5.1)
-  residual   LDG gradient D(U) and residual R(U,Q) (Eqs. 7, 10, 19-32)
-  jacobian   K11, K12, K21 and A by complex step (Sec. 4.1 Eq. 35, Eq. 40)
+  residual   LDG gradient D(U) and residual R(U,Q) (Eqs. 7, 10, 19-32),
+             Neumann sides (Eqs. 29-30), the stabilised trace with C22 and
+             the coupled split residual (R, Q - D(U, Q)) (Eqs. 26, 36)
+  jacobian   K11, K12, K21 and A by complex step (Sec. 4.1 Eq. 35, Eq. 40),
+             the coupled Jacobian [[K11, K12], [-K21, I - K22]]
   solvers    split matvec, masked block-Jacobi / ILU(0), GMRES, Newton-BDF2
-             (Sec. 4.2 Eqs. 39-41)
+             (Sec. 4.2 Eqs. 39-41), DIRK3 and RK4 (Sec. 4.1)
   mlp        line-local MLP forward/backward and Adam (not in the paper)
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
