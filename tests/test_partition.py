@@ -95,11 +95,11 @@ def _worker(rank, ws, port, name, q):
     import torch
     import torch.distributed as dist
 
-    from paper_1204_1533_gb300 import ldg
+    from oracle.residual import Discretization
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     try:
         m, eq, U, layers = _case(name)
-        sw = ldg.ldg_setup_host(m, eq)["sw"]       # the library's global switch function
+        sw = Discretization(m, eq).S               # the oracle's global switch function
         owner = PT.block_partition(m["nodes"].shape[0], ws)
         plan = PT.halo_plan(m, owner, rank, layers, switches=sw)
         res = _local_residual(plan, eq)
