@@ -2,9 +2,10 @@
 3-way element partition, set up as its own sub-mesh (owned elements plus
 two rings of ghosts, cut faces as a Dirichlet tag of their own, the global
 switch function passed in), gives through ldg_residual the rows of its owned
-elements of the global residual, given the ghost states a halo exchange
-delivers (copied here from the global state; the exchange itself is tested
-on CPU ranks in test_partition.py)."""
+elements of the global residual (the oracle's, in extended precision, within
+the residual tolerance 1e-12; and the library's own global rows to 1e-13),
+given the ghost states a halo exchange delivers (copied here from the global
+state; the exchange itself is tested on CPU ranks in test_partition.py)."""
 import numpy as np
 import pytest
 
@@ -38,8 +39,11 @@ def _case(name):
 @pytest.mark.parametrize("name", ["euler2d", "ns2d_unstructured", "ns3d_unstructured"])
 def test_part_residuals_equal_global_rows(L, name):
     import torch
+
+    from oracle.residual import Discretization, full_residual
     m, eq, U, layers = _case(name)
     E = m["nodes"].shape[0]
+    Ro = full_residual(Discretization(m, eq), np.asarray(U, dtype=np.longdouble)).astype(np.float64)
     sw = L.ldg_setup_host(m, eq)["sw"]
     h = L.ldg_setup(m, eq)
     Ug = torch.from_numpy(U).cuda()
@@ -57,6 +61,7 @@ def test_part_residuals_equal_global_rows(L, name):
         L.ldg_residual(hl, Ul, Rl)
         own = plan.local[:plan.n_owned]
         got = Rl.cpu().numpy()[:plan.n_owned]
+        assert np.abs(got - Ro[own]).max() <= 1e-12 * np.abs(Ro).max()
         assert np.abs(got - Rg[own]).max() <= 1e-13 * np.abs(Rg).max()
         seen[own] = True
     assert seen.all()
