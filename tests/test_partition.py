@@ -125,8 +125,9 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("name", ["euler2d", "ns2d_unstructured", "ns3d"])
-def test_partitioned_residual_and_rk4_step_equal_global(name):
+@pytest.mark.parametrize("name,ws", [("euler2d", 2), ("ns2d_unstructured", 2), ("ns3d", 2),
+                                     ("ns2d_unstructured", 3)])
+def test_partitioned_residual_and_rk4_step_equal_global(name, ws):
     import torch.multiprocessing as mp
 
     from oracle.residual import Discretization, full_residual
@@ -134,7 +135,7 @@ def test_partitioned_residual_and_rk4_step_equal_global(name):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, name, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, ws, port, name, q)) for r in range(ws)]
     for p in procs:
         p.start()
     out = [q.get(timeout=300) for _ in procs]
