@@ -195,7 +195,9 @@ def _textbook_dg_1d(x_edges, s, uvals, flux, numflux):
 
 def test_reduces_to_textbook_1d_dg():
     # a state that depends on x only, on an affine mesh: Line-DG equals
-    # standard 1-D DG along the x lines (the scheme's defining property)
+    # standard 1-D DG along the x lines (the scheme's defining property).
+    # This pins the line operator; the numerical flux is the oracle's own
+    # Roe flux here, which tests/test_oracle_fluxes.py pins on its own
     p, nx, ny, L = 3, 5, 3, 10.0
     m = I.structured_mesh((nx, ny), p, (0, 0), (L, 6.0), (True, True))
     x = m["nodes"][..., 0]
