@@ -201,6 +201,9 @@ int ldg_residual(ldg_handle_t* h, const double* U, double* R, void* stream);
  * address; make that first call before any stream capture. All calls share
  * the array, so calls that overlap on the GPU race on it; each call
  * overwrites what it reads, so nothing carries over between calls.
+ * First-order equations need no scratch and never touch the array. For the
+ * stabilised scheme (C22 != 0) the call returns LDG_ERR_UNSUPPORTED, as
+ * ldg_residual does.
  * U, R: device [n_elem][n_c][(p+1)^D], FP64.
  */
 #define LDG_NOALLOC_MAX_Q 1048576
@@ -513,6 +516,17 @@ int ldg_kernel_timer(int enable);
  * unknown kernel or precision or null launches/ms. */
 int ldg_kernel_timer_read(int kernel, int prec, long long* launches, double* ms, double* bytes,
                           double* flops);
+
+/* Benchmark instrumentation; the paper has no counterpart. Enqueues one
+ * kernel of FP64 fused multiply-adds with no memory traffic in its loop
+ * (16 independent chains per thread, 256 threads, 4 blocks per SM of the
+ * current device, `iters` steps per chain) so that a caller timing it with
+ * CUDA events on `stream` gets the FP64 FMA rate the device sustains, the
+ * denominator of the FP64-bound kernels' roofline. sink: device buffer of at
+ * least 4 x (number of SMs) doubles owned by the caller (one value per block
+ * lands there). *fmas (host) receives the number of FMAs enqueued
+ * (2 FLOPs each). LDG_ERR_ARG for iters < 1, a null pointer or a short sink. */
+int ldg_fp64_fma_probe(int32_t iters, double* sink, int64_t sink_len, double* fmas, void* stream);
 
 /* Change the constant viscosity of a Navier-Stokes handle (for sweeps over
  * Reynolds numbers); a retained Jacobian is marked stale. */

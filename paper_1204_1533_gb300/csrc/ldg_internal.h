@@ -78,6 +78,19 @@ struct Geo {
   int64_t E;
 };
 
+// Arnoldi column of GMRES by CGS2 (ldg_ortho.cu): orthogonalises w against
+// the kv basis vectors Vb[0..kv) (stride n) and normalises it. Device
+// scratch: part [GS_PART_LEN], gs [GS_SCRATCH_LEN] doubles. Host col
+// [2 kv + 2]: on return col[0..kv) = Hessenberg entries, col[kv] = the norm
+// before normalisation (0: w lies in the span). Synchronises on st.
+constexpr int GS_KMAX = 32;        // basis vectors per fused sweep
+constexpr int GS_MAX_BASIS = 66;   // largest basis (restart 64 + 2)
+constexpr int GS_MAX_BLOCKS = 320;
+constexpr size_t GS_PART_LEN = (size_t)(GS_KMAX + 1) * GS_MAX_BLOCKS;
+constexpr size_t GS_SCRATCH_LEN = 4 * (GS_MAX_BASIS + 2);
+template <typename V>
+int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, cudaStream_t st);
+
 cudaError_t launch_gradient(const struct ::ldg_handle* h, const double* U, double* Q,
                             cudaStream_t st);
 // D(U, Qs) of the stabilised scheme (C22 != 0): the trace also takes the

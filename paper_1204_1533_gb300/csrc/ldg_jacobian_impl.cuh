@@ -47,6 +47,21 @@ __device__ __forceinline__ float tlift<float>(const Tab& t, int end, int i) { re
 template <>
 __device__ __forceinline__ double tlift<double>(const Tab& t, int end, int i) { return end ? t.L1[i] : t.L0[i]; }
 
+// weight Kd_iq phi_j(xi_q) of a Gauss-point flux derivative in the in-line
+// block, formed in the precision of the derivative arithmetic (an FP64
+// product converted to FP32 would put two FP64-pipe operations into every
+// FP32 multiply-add of the assembly)
+template <typename R>
+__device__ __forceinline__ R kdphi(const Tab& t, int i, int q, int j);
+template <>
+__device__ __forceinline__ float kdphi<float>(const Tab& t, int i, int q, int j) {
+  return t.Kdf[i][q] * t.Phif[q][j];
+}
+template <>
+__device__ __forceinline__ double kdphi<double>(const Tab& t, int i, int q, int j) {
+  return t.Kd[i][q] * t.Phi[q][j];
+}
+
 __device__ __forceinline__ int64_t tile_index(int64_t L, int64_t nk, int64_t k) {
   return ((L >> 5) * nk + k) * 32 + (L & 31);
 }
@@ -82,16 +97,13 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
   const int st = S::stride(d), b0 = S::base(d, l);
   const R* uel = sU + le * tile;
   const R* qel = sQ + le * qtile;
-  Phys pp;
-  pp.gamma = ph.gamma;
-  pp.mu = ph.mu;
-  pp.Pr = ph.Pr;
-  pp.C11 = ph.C11;
-  pp.C11b = ph.C11b;
-  pp.adv[0] = ph.adv[0];
-  pp.adv[1] = ph.adv[1];
-  pp.adv[2] = ph.adv[2];
-  pp.flux = ph.flux;
+  // this line's normals at its Gauss points, converted once into a
+  // per-thread shared slot ([k][thread]: conflict-free)
+  R* sN = sQ + S::EPB * qtile;
+#pragma unroll
+  for (int k = 0; k < NQ * D; ++k) sN[k * S::THREADS + threadIdx.x] = (R)g.ng[L * NQ * D + k];
+  Phys<R> pp;
+  pp.set(ph);
   R ij[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) ij[i] = (R)g.invJ[e * NPE + b0 + i * st];
@@ -181,7 +193,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
     for (int q = 0; q < NQ; ++q) {
       R n[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) n[a] = (R)g.ng[(L * NQ + q) * D + a];
+      for (int a = 0; a < D; ++a) n[a] = sN[(q * D + a) * S::THREADS + threadIdx.x];
       T uq[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -209,7 +221,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
       for (int i = 0; i < N; ++i)
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const R w = (R)(tab.Kd[i][q] * tab.Phi[q][j]);
+          const R w = kdphi<R>(tab, i, q, j);
 #pragma unroll
           for (int c = 0; c < NC; ++c) acc[i][j][c] -= w * f[c].d[0];
         }
@@ -240,7 +252,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
               for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
               viscous_flux_n<EQ, D, T, R>(ui, qq, nv[end], pp, fv);
             }
-            const R pen = (R)ph.C11 * nn[end];
+            const R pen = pp.C11 * nn[end];
 #pragma unroll
             for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
           }
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
             T m2 = ui[1] * ui[1];
 #pragma unroll
             for (int a = 1; a < D; ++a) m2 = m2 + ui[1 + a] * ui[1 + a];
-            const T pr = R(ph.gamma - 1.0) * (ui[D + 1] - R(0.5) * m2 / ui[0]);
+            const T pr = (pp.gamma - R(1)) * (ui[D + 1] - R(0.5) * m2 / ui[0]);
             F[0] = D1<R>::cst(R(0));
 #pragma unroll
             for (int a = 0; a < D; ++a) F[1 + a] = pr * nv[end][a];
@@ -272,7 +284,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
 #pragma unroll
               for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
               viscous_flux_n<EQ, D, T, R>(ub, qq, nv[end], pp, fv);
-              const R pen = (R)ph.C11b * nn[end];
+              const R pen = pp.C11b * nn[end];
 #pragma unroll
               for (int a = 0; a < D; ++a) F[1 + a] = F[1 + a] + fv[1 + a] + pen * (ui[1 + a] - ub[1 + a]);
             }
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
 #pragma unroll
               for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
               viscous_flux_n<EQ, D, T, R>(ui, qq, nv[end], pp, fv);
-              const R pen = (R)ph.C11b * nn[end];
+              const R pen = pp.C11b * nn[end];
 #pragma unroll
               for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
             }
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
       for (int q = 0; q < NQ; ++q) {
         R n[D], uq[NC], fv[NC];
 #pragma unroll
-        for (int a = 0; a < D; ++a) n[a] = (R)g.ng[(L * NQ + q) * D + a];
+        for (int a = 0; a < D; ++a) n[a] = sN[(q * D + a) * S::THREADS + threadIdx.x];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           R s = 0;
@@ -355,7 +367,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
         for (int i = 0; i < N; ++i)
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            const R w = (R)(tab.Kd[i][q] * tab.Phi[q][j]);
+            const R w = kdphi<R>(tab, i, q, j);
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[i][j][c] -= w * fv[c];
           }
@@ -472,7 +484,8 @@ cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, 
   using S = Shape<D, P>;
   constexpr int NC = NComp<EQ, D>::value;
   constexpr bool VISC = IsViscous<EQ>::value;
-  const size_t smem = (size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0)) * sizeof(R);
+  const size_t smem = ((size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0)) +
+                       (size_t)S::THREADS * S::NQ * D) * sizeof(R);
   auto kern = k_jacobian<D, P, NC, EQ, R>;
   cudaError_t err = set_smem_once(kern, smem);
   if (err != cudaSuccess) return err;

@@ -24,10 +24,26 @@ enum { EQ_POISSON = 0, EQ_EULER = 1, EQ_NS = 2, EQ_ADV = 3 };
 enum { FLUX_ROE = 0, FLUX_LF = 1 };
 enum { BC_DIRICHLET = 0, BC_WALL = 1, BC_NEUMANN = 2 };
 
+// physical constants at the precision R of the flux arithmetic (converted
+// once per thread: on this part an FP64 -> FP32 conversion costs as much as an
+// FP64 multiply-add, so FP32 derivative code must not convert per call)
+template <typename R>
 struct Phys {
-  double gamma, mu, Pr, C11, C11b;
-  double adv[3];
+  R gamma, mu, Pr, C11, C11b;
+  R adv[3];
   int flux;
+  template <typename A>
+  __device__ __forceinline__ void set(const A& ph) {
+    gamma = R(ph.gamma);
+    mu = R(ph.mu);
+    Pr = R(ph.Pr);
+    C11 = R(ph.C11);
+    C11b = R(ph.C11b);
+    adv[0] = R(ph.adv[0]);
+    adv[1] = R(ph.adv[1]);
+    adv[2] = R(ph.adv[2]);
+    flux = ph.flux;
+  }
 };
 
 template <int EQ, int D>
@@ -229,13 +245,13 @@ __device__ __forceinline__ void ns_visc_flux_n(const T* u, const T* q, const R* 
 
 // inviscid part of F . n for the equation set
 template <int EQ, int D, typename T, typename R>
-__device__ __forceinline__ void inviscid_flux_n(const T* u, const R* n, const Phys& ph, T* f) {
+__device__ __forceinline__ void inviscid_flux_n(const T* u, const R* n, const Phys<R>& ph, T* f) {
   if constexpr (EQ == EQ_EULER || EQ == EQ_NS) {
-    euler_flux_n<D, T, R>(u, n, R(ph.gamma) - R(1.0), f);
+    euler_flux_n<D, T, R>(u, n, ph.gamma - R(1.0), f);
   } else if constexpr (EQ == EQ_ADV) {
-    R an = R(ph.adv[0]) * n[0];
+    R an = ph.adv[0] * n[0];
 #pragma unroll
-    for (int b = 1; b < D; ++b) an += R(ph.adv[b]) * n[b];
+    for (int b = 1; b < D; ++b) an += ph.adv[b] * n[b];
     f[0] = an * u[0];
   } else {
     f[0] = T(0.0);
@@ -244,16 +260,16 @@ __device__ __forceinline__ void inviscid_flux_n(const T* u, const R* n, const Ph
 
 template <int EQ, int D, typename T, typename R>
 __device__ __forceinline__ void inviscid_numflux(const T* uo, const T* ui, const R* n,
-                                                 const Phys& ph, T* f) {
+                                                 const Phys<R>& ph, T* f) {
   if constexpr (EQ == EQ_EULER || EQ == EQ_NS) {
     if (ph.flux == FLUX_ROE)
-      roe_flux<D, T, R>(uo, ui, n, R(ph.gamma), f);
+      roe_flux<D, T, R>(uo, ui, n, ph.gamma, f);
     else
-      lf_flux<D, T, R>(uo, ui, n, R(ph.gamma), f);
+      lf_flux<D, T, R>(uo, ui, n, ph.gamma, f);
   } else if constexpr (EQ == EQ_ADV) {
-    R an = R(ph.adv[0]) * n[0];
+    R an = ph.adv[0] * n[0];
 #pragma unroll
-    for (int b = 1; b < D; ++b) an += R(ph.adv[b]) * n[b];
+    for (int b = 1; b < D; ++b) an += ph.adv[b] * n[b];
     f[0] = (an >= R(0.0)) ? an * ui[0] : an * uo[0];
   } else {
     f[0] = T(0.0);
@@ -261,10 +277,10 @@ __device__ __forceinline__ void inviscid_numflux(const T* uo, const T* ui, const
 }
 
 template <int EQ, int D, typename T, typename R>
-__device__ __forceinline__ void viscous_flux_n(const T* u, const T* q, const R* n, const Phys& ph,
+__device__ __forceinline__ void viscous_flux_n(const T* u, const T* q, const R* n, const Phys<R>& ph,
                                                T* f) {
   if constexpr (EQ == EQ_NS) {
-    ns_visc_flux_n<D, T, R>(u, q, n, R(ph.gamma), R(ph.mu), R(ph.Pr), f);
+    ns_visc_flux_n<D, T, R>(u, q, n, ph.gamma, ph.mu, ph.Pr, f);
   } else if constexpr (EQ == EQ_POISSON) {
     T s = q[0] * n[0];
 #pragma unroll

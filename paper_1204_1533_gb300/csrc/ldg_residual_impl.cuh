@@ -203,16 +203,8 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
   if constexpr (VISC)
     for (int k = threadIdx.x; k < ne * qtile; k += blockDim.x) sQ[k] = Q[e0 * qtile + k];
   __syncthreads();
-  Phys pp;
-  pp.gamma = ph.gamma;
-  pp.mu = ph.mu;
-  pp.Pr = ph.Pr;
-  pp.C11 = ph.C11;
-  pp.C11b = ph.C11b;
-  pp.adv[0] = ph.adv[0];
-  pp.adv[1] = ph.adv[1];
-  pp.adv[2] = ph.adv[2];
-  pp.flux = ph.flux;
+  Phys<double> pp;
+  pp.set(ph);
   const int le = threadIdx.x / S::TPE, rr = threadIdx.x % S::TPE;
   if (le < ne) {
     const int d = rr / S::NL, l = rr % S::NL;

@@ -59,100 +59,6 @@ __global__ void k_reduce_rows(const double* __restrict__ part, int nblk, double*
   }
 }
 
-// Fused Gram-Schmidt sweeps over up to OKMAX basis vectors V_j0 .. V_j0+kk-1,
-// one pass each, w read once per element:
-//   OrthoOp::Dots       part[j][blk] = sum_i V_j[i] w[i]
-//   OrthoOp::UpdateDots w -= sum_j h_j V_j, then part[j][blk] = sum_i V_j[i] w[i]
-//   OrthoOp::UpdateNorm w -= sum_j h_j V_j, then part[0][blk] = sum_i w[i]^2
-//   OrthoOp::Update     w -= sum_j h_j V_j
-// Products and per-thread sums are in the vector precision V (FP32 for the
-// FP32 Krylov basis: its dot products are FP32 work), block partials in FP64.
-constexpr int OKMAX = 32;
-constexpr int ORTHO_BLOCKS = 304;  // partial-sum rows: two blocks of 256 threads per SM
-// FP64 sweeps over more than 16 vectors hold up to 64 doubles per thread
-// (one block per SM fits); each thread keeps KC independent loads in
-// flight, so one block per SM still streams at full bandwidth
-template <typename V, int KC>
-constexpr int ortho_blocks() { return (sizeof(V) == 8 && KC > 16) ? ORTHO_BLOCKS / 2 : ORTHO_BLOCKS; }
-enum class OrthoOp { Dots, UpdateDots, UpdateNorm, Update };
-
-// KC: vectors handled per thread, kk rounded up to a multiple of 8 (the
-// loops run to KC with j < kk guards; predicated-off FP64 operations still
-// take issue slots of the narrow FP64 pipe, so KC tracks kk)
-template <typename V, OrthoOp OP, int KC>
-__global__ void __launch_bounds__(256) k_ortho(const V* __restrict__ Vb, int64_t n, int kk, V* __restrict__ w,
-                                               const double* __restrict__ h, double* __restrict__ part) {
-  constexpr bool UPD = OP != OrthoOp::Dots;
-  constexpr bool DOTS = OP == OrthoOp::Dots || OP == OrthoOp::UpdateDots;
-  constexpr bool NORM = OP == OrthoOp::UpdateNorm;
-  __shared__ V hs[KC];
-  __shared__ double red[8][KC];
-  if (UPD && threadIdx.x < kk) hs[threadIdx.x] = (V)h[threadIdx.x];
-  __syncthreads();
-  V acc[KC];
-#pragma unroll
-  for (int j = 0; j < KC; ++j) acc[j] = V(0);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    V v[KC];
-#pragma unroll
-    for (int j = 0; j < KC; ++j) v[j] = j < kk ? Vb[(int64_t)j * n + i] : V(0);
-    V s = w[i];
-    if constexpr (UPD) {
-      V p[4] = {V(0), V(0), V(0), V(0)};  // four independent chains
-#pragma unroll
-      for (int j = 0; j < KC; ++j)
-        if (j < kk) p[j & 3] += hs[j] * v[j];
-      s -= (p[0] + p[1]) + (p[2] + p[3]);
-      w[i] = s;
-    }
-    if constexpr (DOTS) {
-#pragma unroll
-      for (int j = 0; j < KC; ++j)
-        if (j < kk) acc[j] += v[j] * s;
-    }
-    if constexpr (NORM) acc[0] += s * s;
-  }
-  if constexpr (DOTS || NORM) {
-    const int nd = NORM ? 1 : kk;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    if constexpr (NORM) {
-      double x = (double)acc[0];
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) red[wp][0] = x;
-    } else {
-      // warp sums of KC values by recursive halving: each exchange step
-      // halves the values a lane holds, so a lane ends with the warp total
-      // of value (lane mod KP) after KP - 1 + log2(32 / KP) additions (a
-      // butterfly per value would take 5 KC); every FP64 addition of a warp
-      // costs the narrow FP64 pipe
-      constexpr int KP = KC <= 8 ? 8 : (KC <= 16 ? 16 : 32);
-      double v[KP];
-#pragma unroll
-      for (int j = 0; j < KP; ++j) v[j] = j < KC ? (double)acc[j] : 0.0;
-#pragma unroll
-      for (int half = KP / 2; half >= 1; half >>= 1) {
-        const bool up = (lane & half) != 0;
-#pragma unroll
-        for (int k = 0; k < half; ++k) {
-          const double keep = up ? v[half + k] : v[k];
-          const double send = up ? v[k] : v[half + k];
-          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-        }
-      }
-      double x = v[0];
-#pragma unroll
-      for (int o = KP; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane < KP && lane < nd) red[wp][lane] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < nd) {
-      double x = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x += red[k][threadIdx.x];
-      part[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = x;
-    }
-  }
-}
-
 // dst = sum_j y_j V_j  (y on the device)
 template <typename V>
 __global__ void k_combine(V* __restrict__ dst, const V* __restrict__ Vb, const double* __restrict__ y, int k,
@@ -212,19 +118,19 @@ struct Work {
   void *z, *t;                                // precision of the basis
   double* part;                               // [ (m+2) * MDOT_BLOCKS ]
   double* hcol;                               // [m+2]
-  double* hacc;                               // [m+2]
+  double* hacc;                               // Gram-Schmidt scratch [GS_SCRATCH_LEN]
   double* y;                                  // [m+1]
 };
 
 static size_t part_len(int m) {
-  const size_t a = (size_t)(m + 2) * MDOT_BLOCKS, b = (size_t)OKMAX * ORTHO_BLOCKS;
+  const size_t a = (size_t)(m + 2) * MDOT_BLOCKS, b = GS_PART_LEN;
   return a > b ? a : b;
 }
 
 static size_t work_bytes(const ldg_handle* h, int m, int vbytes) {
   const size_t N = (size_t)h->ndof;
   return 6 * N * 8 + (size_t)(m + 1) * N * vbytes + 2 * N * vbytes + part_len(m) * 8 +
-         3 * (size_t)(m + 2) * 8 + 64 * 256;  // plus 256-byte alignment of each piece
+         (2 * (size_t)(m + 2) + GS_SCRATCH_LEN) * 8 + 64 * 256;  // plus 256-byte alignment of each piece
 }
 
 static int get_work(ldg_handle* h, int m, int vbytes, Work& w) {
@@ -254,7 +160,7 @@ static int get_work(ldg_handle* h, int m, int vbytes, Work& w) {
   w.t = take(N * vbytes);
   w.part = (double*)take(part_len(m) * 8);
   w.hcol = (double*)take((size_t)(m + 2) * 8);
-  w.hacc = (double*)take((size_t)(m + 2) * 8);
+  w.hacc = (double*)take(GS_SCRATCH_LEN * 8);
   w.y = (double*)take((size_t)(m + 2) * 8);
   return (size_t)(p - (char*)h->ws) <= h->ws_bytes ? LDG_OK : LDG_ERR_CUDA;
 }
@@ -271,70 +177,6 @@ static cudaError_t mdot(const V* Vb, int k, int64_t n, const V* w, double* part,
   return cudaGetLastError();
 }
 
-// One fused sweep (see k_ortho) over basis vectors j0 .. j0+kk-1 (kk <= OKMAX);
-// dot products or the norm land in dev[] (and are added to accum[]).
-template <typename V, OrthoOp OP>
-static cudaError_t ortho(const V* Vb, int kk, int64_t n, V* w, const double* hin, double* part, double* dev,
-                         double* accum, cudaStream_t st) {
-  constexpr bool UPD = OP != OrthoOp::Dots;
-  const double vsz = sizeof(V), nn = (double)n;
-  const double fma_per = OP == OrthoOp::UpdateDots ? 2.0 * kk : (OP == OrthoOp::UpdateNorm ? kk + 1.0 : kk);
-  int nb;
-  {  // the timed region is the sweep; the row reduction follows
-    TimedScope tl(KT_ORTHO, sizeof(V) == 4 ? LDG_PREC_FP32 : LDG_PREC_FP64, st,
-                  nn * vsz * (kk + 1 + (UPD ? 1 : 0)), 2.0 * nn * fma_per);
-    if (kk <= 8) {
-      nb = ortho_blocks<V, 8>();
-      k_ortho<V, OP, 8><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-    } else if (kk <= 16) {
-      nb = ortho_blocks<V, 16>();
-      k_ortho<V, OP, 16><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-    } else if (kk <= 24) {
-      nb = ortho_blocks<V, 24>();
-      k_ortho<V, OP, 24><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-    } else {
-      nb = ortho_blocks<V, OKMAX>();
-      k_ortho<V, OP, OKMAX><<<nb, 256, 0, st>>>(Vb, n, kk, w, hin, part);
-    }
-  }
-  count_launch();
-  if constexpr (OP != OrthoOp::Update) {
-    const int nd = OP == OrthoOp::UpdateNorm ? 1 : kk;
-    k_reduce_rows<<<nd, 256, 0, st>>>(part, nb, dev, accum);
-    count_launch();
-  }
-  return cudaGetLastError();
-}
-
-// Classical Gram-Schmidt with one re-orthogonalisation of w against
-// V_0 .. V_{k}: hacc[0..k] receives the summed coefficients, hacc[k+1] the
-// squared norm of the result. With up to OKMAX vectors this is three fused
-// sweeps (dots; update + dots; update + norm), beyond that chunked sweeps.
-template <typename V>
-static cudaError_t cgs2(const V* Vb, int kv, int64_t n, V* w, const Work& ws, cudaStream_t st) {
-  cudaError_t e;
-  if (kv <= OKMAX) {
-    if ((e = ortho<V, OrthoOp::Dots>(Vb, kv, n, w, nullptr, ws.part, ws.hcol, ws.hacc, st))) return e;
-    if ((e = ortho<V, OrthoOp::UpdateDots>(Vb, kv, n, w, ws.hcol, ws.part, ws.hcol, ws.hacc, st))) return e;
-    return ortho<V, OrthoOp::UpdateNorm>(Vb, kv, n, w, ws.hcol, ws.part, ws.hacc + kv, nullptr, st);
-  }
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int j0 = 0; j0 < kv; j0 += OKMAX) {
-      const int kk = kv - j0 < OKMAX ? kv - j0 : OKMAX;
-      if ((e = ortho<V, OrthoOp::Dots>(Vb + (int64_t)j0 * n, kk, n, w, nullptr, ws.part, ws.hcol + j0,
-                                       ws.hacc + j0, st)))
-        return e;
-    }
-    for (int j0 = 0; j0 < kv; j0 += OKMAX) {
-      const int kk = kv - j0 < OKMAX ? kv - j0 : OKMAX;
-      if ((e = ortho<V, OrthoOp::Update>(Vb + (int64_t)j0 * n, kk, n, w, ws.hcol + j0, ws.part, nullptr,
-                                         nullptr, st)))
-        return e;
-    }
-  }
-  return ortho<V, OrthoOp::Dots>(w, 1, n, w, nullptr, ws.part, ws.hacc + kv, nullptr, st);
-}
-
 // Right-preconditioned GMRES(m) on (I - adt A) x = b for vectors of type V;
 // b is overwritten; x receives the solution (zero initial guess).
 template <typename V>
@@ -344,7 +186,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
   V* Vb = (V*)w.Vb;
   V* z = (V*)w.z;
   V* t = (V*)w.t;
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(m + 2);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), hc(2 * (size_t)m + 4);
   // beta = ||b||
   if (mdot<V>(b, 1, n, b, w.part, w.hcol, nullptr, st) != cudaSuccess) return LDG_ERR_CUDA;
   double bb = 0;
@@ -368,17 +210,13 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
     V* vn = Vb + (int64_t)(k + 1) * n;
     if (launch_precond_apply(h, h->Pn, vk, z, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
     if (launch_jacvec(h, h->Jn, 1.0, -adt, z, vn, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
-    // classical Gram-Schmidt, twice
-    LDG_CUDA_TRY(cudaMemsetAsync(w.hacc, 0, (k + 2) * sizeof(double), st));
-    if (cgs2<V>(Vb, k + 1, n, vn, w, st) != cudaSuccess) return LDG_ERR_CUDA;
-    LDG_CUDA_TRY(cudaMemcpyAsync(hc.data(), w.hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LDG_CUDA_TRY(cudaStreamSynchronize(st));
+    // classical Gram-Schmidt, twice; vn normalised on return
+    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), st);
+    if (grc) return grc;
     for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
-    const double hn = std::sqrt(hc[k + 1]);
+    const double hn = hc[k + 1];
     if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
     H[(size_t)(k + 1) * m + k] = hn;
-    if (hn > 0) k_scale_to<V, V><<<grid_for(n), 256, 0, st>>>(vn, vn, 1.0 / hn, n);
-    count_launch();
     for (int j = 0; j < k; ++j) {
       const double a = H[(size_t)j * m + k], c = H[(size_t)(j + 1) * m + k];
       H[(size_t)j * m + k] = cs[j] * a + sn[j] * c;
@@ -959,10 +797,9 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
       col[e] = cc;
       if (cc + 1 > c->ncolors) c->ncolors = cc + 1;
     }
-    const size_t parts = (size_t)(m + 2) * MDOT_BLOCKS > (size_t)OKMAX * ORTHO_BLOCKS
-                             ? (size_t)(m + 2) * MDOT_BLOCKS
-                             : (size_t)OKMAX * ORTHO_BLOCKS;
-    const size_t nbuf = (size_t)M * (5 + m + 1) + (size_t)N * D + parts + 3 * (size_t)(m + 2);
+    const size_t parts = (size_t)(m + 2) * MDOT_BLOCKS > GS_PART_LEN ? (size_t)(m + 2) * MDOT_BLOCKS
+                                                                      : GS_PART_LEN;
+    const size_t nbuf = (size_t)M * (5 + m + 1) + (size_t)N * D + parts + 2 * (size_t)(m + 2) + GS_SCRATCH_LEN;
     LDG_CUDA_TRY(cudaMalloc((void**)&c->color, E * sizeof(int32_t)));
     LDG_CUDA_TRY(cudaMalloc((void**)&c->Binv, (size_t)E * B * B * sizeof(double)));
     LDG_CUDA_TRY(cudaMalloc((void**)&c->buf, nbuf * sizeof(double)));
@@ -977,7 +814,7 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
     c->Gt = p; p += (size_t)N * D;
     c->part = p; p += parts;
     c->hcol = p; p += m + 2;
-    c->hacc = p; p += m + 2;
+    c->hacc = p; p += GS_SCRATCH_LEN;
     c->y = p;
     LDG_CUDA_TRY(cudaStreamSynchronize(st));
   }
@@ -1021,7 +858,7 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
   if ((rc = cpl_phi(h, c->x, c->phi, c->Gt, st))) return rc;
   if ((rc = nrm(c->phi, &res0))) return rc;
   stats->res0 = res = res0;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hc(m + 2);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hc(2 * (size_t)m + 4);
   for (int cyc = 0; cyc < max_cycles && res > rtol * res0; ++cyc) {
     stats->newton_its += 1;
     // V_0 = -Phi(x) / ||Phi(x)||
@@ -1037,17 +874,10 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
       k_cpl_apply<<<(unsigned)E, 128, 0, st>>>(c->z, vk, c->Binv, B, npe, D, N);
       count_launch();
       if ((rc = cpl_phi(&hh, c->z, vn, c->Gt, st))) return rc;
-      LDG_CUDA_TRY(cudaMemsetAsync(c->hacc, 0, (k + 2) * sizeof(double), st));
-      if (cgs2<double>(c->Vb, k + 1, M, vn, w, st) != cudaSuccess) return LDG_ERR_CUDA;
-      LDG_CUDA_TRY(cudaMemcpyAsync(hc.data(), c->hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      LDG_CUDA_TRY(cudaStreamSynchronize(st));
+      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), st))) return rc;
       for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
-      const double hn = std::sqrt(hc[k + 1]);
+      const double hn = hc[k + 1];
       if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
-      if (hn > 0) {
-        k_scale_to<double, double><<<grid_for(M), 256, 0, st>>>(vn, vn, 1.0 / hn, M);
-        count_launch();
-      }
       for (int j = 0; j < k; ++j) {
         const double a = H[(size_t)j * m + k], b = H[(size_t)(j + 1) * m + k];
         H[(size_t)j * m + k] = cs[j] * a + sn[j] * b;

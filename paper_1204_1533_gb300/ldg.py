@@ -90,6 +90,7 @@ _SIGS = {
     "ldg_kernel_timer_read": [C.c_int32, C.c_int32, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "ldg_residual_noalloc": [_P, _P, _P, _P],
+    "ldg_fp64_fma_probe": [C.c_int32, _P, C.c_int64, C.POINTER(C.c_double), _P],
     "ldg_set_viscosity": [_P, C.c_double],
     "ldg_mlp_create": [C.c_int32, C.c_int32, C.POINTER(_P)],
     "ldg_mlp_destroy": [_P],
@@ -443,6 +444,15 @@ def ldg_kernel_timer_read(kernel, prec):
     _check(lib().ldg_kernel_timer_read(kernel, prec, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)),
            "ldg_kernel_timer_read")
     return n.value, ms.value, by.value, fl.value
+
+
+def ldg_fp64_fma_probe(iters, sink, stream=None):
+    """Enqueue the FP64 FMA-throughput kernel (see ldg.h); returns the number
+    of FMAs it performs. sink: CUDA float64 tensor of >= 4 x SMs values."""
+    f = C.c_double()
+    _check(lib().ldg_fp64_fma_probe(int(iters), _dptr(sink), sink.numel(), C.byref(f), _stream(stream)),
+           "ldg_fp64_fma_probe")
+    return f.value
 
 
 def ldg_residual_noalloc(h, U, R, stream=None):

@@ -130,21 +130,22 @@ def halo_plan(mesh, owner, rank, layers, adjacency=None, switches=None):
 def halo_exchange(U_local, plan, group=None):
     """Fill the ghost blocks of U_local [n_local, ...] (a torch tensor; the
     owned blocks must be current) from their owners. Messages are whole
-    element blocks in increasing global element id; every pair of ranks
-    posts its sends before its receives complete (non-blocking)."""
+    element blocks in increasing global element id. All sends and receives
+    of the exchange are posted as one group (batch_isend_irecv): under NCCL
+    point-to-point calls issued one by one queue on each pair's stream, and
+    two ranks that both send first could wait on each other; a group lets the
+    backend match them."""
     import torch.distributed as dist
-    reqs, bufs = [], []
+    ops, recvd = [], []
     for dst, rows in sorted(plan.send.items()):
-        buf = U_local[rows].contiguous()
-        bufs.append(buf)
-        reqs.append(dist.isend(buf, dst, group=group))
-    recvd = []
+        ops.append(dist.P2POp(dist.isend, U_local[rows].contiguous(), dst, group=group))
     for src, rows in sorted(plan.recv.items()):
         buf = U_local.new_empty((len(rows),) + tuple(U_local.shape[1:]))
         recvd.append((rows, buf))
-        reqs.append(dist.irecv(buf, src, group=group))
-    for r in reqs:
-        r.wait()
+        ops.append(dist.P2POp(dist.irecv, buf, src, group=group))
+    if ops:
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
     for rows, buf in recvd:
         U_local[rows] = buf
     return U_local
@@ -162,10 +163,19 @@ def partitioned_residual(U_owned, plan, local_residual, U_local=None, group=None
     return local_residual(U_local)[:plan.n_owned]
 
 
-def global_norm(x_owned, group=None):
-    """||x||_2 over all ranks: one all-reduce of the squared norms."""
+def global_norm(x_owned, group=None, local_sq=None):
+    """||x||_2 over all ranks: each rank's sum of squares of its owned
+    entries, then one all-reduce. local_sq(x) -> float gives that sum on the
+    rank (on a GPU: ldg_norm2 of the owned slice, squared); by default it is
+    taken on the tensor's own device."""
+    import math
+
     import torch
     import torch.distributed as dist
-    s = (x_owned.double() ** 2).sum().reshape(1)
+    if local_sq is None:
+        sq = float((x_owned.double() ** 2).sum())
+    else:
+        sq = float(local_sq(x_owned))
+    s = torch.tensor([sq], dtype=torch.float64, device=x_owned.device)
     dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
-    return float(torch.sqrt(s))
+    return math.sqrt(float(s))
