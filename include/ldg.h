@@ -98,7 +98,11 @@ typedef struct {
  *   kind, flux        LDG_EQ_*, LDG_FLUX_*
  *   gamma, mu, Pr     ideal gas ratio, constant viscosity, Prandtl number
  *   C11, C11_b        LDG penalty at interior faces (0 = minimal dissipation)
- *                     and at Dirichlet/wall boundaries (> 0), Eqs. 25, 27
+ *                     and at Dirichlet/wall boundaries (> 0), Eqs. 25, 27:
+ *                     an interior line end's F^.n (non-unit n of Eq. 7) gains
+ *                     C11 (u_in - u_out), a penalty per unit reference length
+ *                     (C11 / h physically); a boundary end gains
+ *                     C11_b |n| (u_in - g_D)
  *   adv[3]            advection velocity (LDG_EQ_ADVECTION)
  *   n_bc, bc_kind     bc_kind[tag] = LDG_BC_* for boundary tags 0..n_bc-1
  *   g_D               [n_elem][n_c][(p+1)^D] Dirichlet data (read at boundary
@@ -312,7 +316,16 @@ typedef struct {
   double gmres_tol;      /* relative tolerance of each linear solve           */
   int32_t stall_rebuild; /* 1: also rebuild K, P when a Newton step fails to
                             halve ||G|| (an addition to the paper's policy)   */
+  int32_t forcing;       /* LDG_FORCING_*: relative tolerance of each linear
+                            solve (not in the paper)                          */
 } ldg_solver_opts_t;
+
+#define LDG_FORCING_FIXED 0  /* every linear solve to gmres_tol ||G||          */
+#define LDG_FORCING_TARGET 1 /* to max(gmres_tol, 0.5 target / ||G||) ||G||
+                                (target = rtol ||G(U^n)||): no solve reduces
+                                ||G|| further than the stopping rule needs, so
+                                the linear work follows the decades between
+                                the start and the target                      */
 
 typedef struct {
   int32_t newton_its;

@@ -14,7 +14,9 @@ with the trace u^ of Eq. 20, and q = (1/J) sum_d d^(d) (Eq. 32).
 Numerical fluxes (Sec. 3, Eqs. 25-28, C12 = n S/2, C22 = 0):
   interior, switch S = S^+-_d of this element and end:
       F^vis . n = F^vis(outside) . n  if S = +1, F^vis(inside) . n if S = -1,
-                  plus C11 |n| (u_in - u_out)        (dissipative sign)
+                  plus C11 (u_in - u_out)            (dissipative sign; with the
+                  non-unit normal n of Eq. 7 this is a penalty per unit
+                  reference length, C11 / h in physical units)
       u^        = inside if S = +1, outside if S = -1
   Dirichlet boundary (Eqs. 27-28):
       F^vis . n = F^vis(u_in, q_in) . n + C11_b |n| (u_in - g_D),  u^ = g_D,
@@ -225,7 +227,8 @@ def residual(disc, U, Q=None, gD=None, source=None):
                 Sw = disc.S[:, d, end][:, None]
                 fv_out = ph.viscous_flux_n(eq, u_out, q_out, n)
                 fv_in = ph.viscous_flux_n(eq, u_in, q_in, n)
-                Fv = np.where(Sw == 1, fv_out, fv_in) + disc.C11 * ph.norm(n) * (u_in - u_out)
+                # interior penalty per unit reference length (C11 / h physically)
+                Fv = np.where(Sw == 1, fv_out, fv_in) + disc.C11 * (u_in - u_out)
                 Fh = Fh + Fv
             if np.any(bnd):
                 kinds = _bc_kind(disc, g)

@@ -174,16 +174,20 @@ struct ldg_jac {
   void* K21 = nullptr;
   void* Kw = nullptr;     // wall ends: energy row of the wall-state derivative, 2 n_c per line (tiles)
   void* gbuf = nullptr;   // K21 x workspace [E][nc][D][npe] in the vector precision (double)
+  void* ucvt = nullptr;   // FP32 Jacobians: FP32 copies of U [ndof] and Q [ndof D] for the assembly
 };
 
-// Element-block ILU(0) factors [E][npe][Dp+1][nc][nc] and inverted diagonal
-// blocks of U [E][npe][nc][nc], at the Jacobian's precision.
+// Element-block ILU(0) factors [E][npe][Dp+1][nc][nc] at the Jacobian's
+// precision: L below the diagonal, U above it, and in each row's diagonal
+// slot the inverse of U's diagonal block (what the triangular solves use);
+// the diagonal blocks U_ii themselves [E][npe][nc][nc] are kept aside for
+// the export.
 struct ldg_pc {
   ldg_handle* h = nullptr;
   int prec = 0;
   bool built = false;
   void* F = nullptr;
-  void* Dinv = nullptr;
+  void* Udiag = nullptr;
 };
 
 namespace ldg {

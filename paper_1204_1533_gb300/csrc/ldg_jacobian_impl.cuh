@@ -5,13 +5,14 @@
 //   dr_i/du_j     = -sum_q Kd_iq (dF.n/du)(xi_q) phi_j(xi_q)
 //                   + L1_i dF^+/du_in [j = p] + L0_i dF^-/du_in [j = 0]
 //   dr_i/du_out,e = L_e,i dF^e/du_out                      (face block)
-// and likewise for q. One thread per line; columns are produced one at a
-// time by forward-mode derivatives seeded on a single component (Dual<R,1>),
-// which keeps the (p+1)^2 n_c accumulators of a column in registers. The
-// viscous flux is linear in q, so K12's columns are flux evaluations with
-// unit q vectors. Values are computed at precision R (float: the mixed
-// path, FP32 values from the FP64 state; double: the all-FP64 path) and
-// stored entry-major in 32-line tiles so each warp's stores are coalesced.
+// and likewise for q. The pointwise derivative matrices are evaluated once
+// per Gauss point and line end (forward-mode dual numbers over all n_c
+// components; the viscous flux is linear in q, so its q-derivatives are
+// flux evaluations with unit q vectors) and contracted with the 1-D tables
+// row by row (k_jacobian below). Values are computed at precision R (float:
+// the mixed path, from FP32 copies of the FP64 state; double: the all-FP64
+// path) and stored entry-major in 32-line tiles so each warp's stores are
+// coalesced.
 #pragma once
 #include "ldg_residual_impl.cuh"
 
@@ -66,358 +67,446 @@ __device__ __forceinline__ int64_t tile_index(int64_t L, int64_t nk, int64_t k) 
   return ((L >> 5) * nk + k) * 32 + (L & 31);
 }
 
-template <int D, int P, int NC, int EQ, typename R>
-__global__ void __launch_bounds__(Shape<D, P>::THREADS)
-    k_jacobian(const double* __restrict__ U, const double* __restrict__ Q, R* __restrict__ K11,
-               R* __restrict__ K12, R* __restrict__ Kw, Geo g, Tab tab, PhysArgs ph) {
-  using S = Shape<D, P>;
-  using T = Dual<R, 1>;
-  constexpr int N = S::N, NPE = S::NPE, NQ = S::NQ, NCD = NC * D;
-  constexpr bool VISC = IsViscous<EQ>::value;
-  constexpr int tile = NC * NPE;
-  constexpr int qtile = VISC ? NCD * NPE : 0;
-  constexpr int64_t NK11 = (N * N + 2 * N) * NC * NC;
-  constexpr int64_t NK12 = VISC ? (N * N + N) * NC * NCD : 1;
-  constexpr int OFF11 = N * N * NC * NC;
-  constexpr int OFF12 = N * N * NC * NCD;
-  extern __shared__ unsigned char smraw[];
-  R* sU = reinterpret_cast<R*>(smraw);
-  R* sQ = sU + S::EPB * tile;
-  const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
-  const int ne = (int)min((int64_t)S::EPB, g.E - e0);
-  for (int k = threadIdx.x; k < ne * tile; k += blockDim.x) sU[k] = (R)U[e0 * tile + k];
-  if constexpr (VISC)
-    for (int k = threadIdx.x; k < ne * qtile; k += blockDim.x) sQ[k] = (R)Q[e0 * qtile + k];
-  __syncthreads();
-  const int le = threadIdx.x / S::TPE, rr = threadIdx.x % S::TPE;
-  if (le >= ne) return;
-  const int d = rr / S::NL, l = rr % S::NL;
-  const int64_t e = e0 + le;
-  const int64_t L = (e * D + d) * S::NL + l;
-  const int st = S::stride(d), b0 = S::base(d, l);
-  const R* uel = sU + le * tile;
-  const R* qel = sQ + le * qtile;
-  // this line's normals at its Gauss points, converted once into a
-  // per-thread shared slot ([k][thread]: conflict-free)
-  R* sN = sQ + S::EPB * qtile;
+// ---------------------------------------------------------------------------
+// Tiled assembly: one block per 32-line tile of the K storage, two rounds
+// (K11, then K12 for second-order equations), each in two phases.
+//   Phase A, one thread per (line, Gauss point q) and (line, end): the
+//   pointwise derivative matrices, written to shared memory lane-minor:
+//     K11 round: A_q = d(F.n_q)/du (forward mode, all n_c directions in one
+//                evaluation), B_end,side = dF^_end/du_inside / du_outside
+//     K12 round: A_q = d(F^vis.n_q)/dq (F^vis is linear in q: one real
+//                evaluation per unit q vector), C_end = the line end's
+//                viscous-flux derivative when it enters the in-line block,
+//                Cf = the face block's (the end whose switch takes the
+//                viscous flux from outside)
+//   Phase B, one thread per (line, row i, block column): the contraction
+//     dr_i/du_j = -sum_q Kd_iq phi_j(xi_q) A_q + L_end,i B_end,in [j = end]
+//   and the store; a warp covers the 32 lines of the tile for one entry, so
+//   every store is one 128-byte (FP32) segment.
+// The state and gradient arrive at the arithmetic precision R (FP32 copies
+// for the FP32 Jacobian), so the derivative arithmetic is pure R; only the
+// metric terms are converted, once per use.
+// ---------------------------------------------------------------------------
+template <typename R, int M>
+__device__ __forceinline__ Dual<R, M> dseed(R v, int k) {
+  Dual<R, M> x(0.0);
+  x.v = v;
 #pragma unroll
-  for (int k = 0; k < NQ * D; ++k) sN[k * S::THREADS + threadIdx.x] = (R)g.ng[L * NQ * D + k];
+  for (int i = 0; i < M; ++i) x.d[i] = (i == k) ? R(1) : R(0);
+  return x;
+}
+template <typename R, int M>
+__device__ __forceinline__ Dual<R, M> dconst(R v) {
+  Dual<R, M> x(0.0);
+  x.v = v;
+  return x;
+}
+
+template <int D, int P, int NC, int EQ, typename R>
+struct JacTile {
+  using S = Shape<D, P>;
+  static constexpr int N = S::N, NQ = S::NQ, NPE = S::NPE, NL = S::NL, NCD = NC * D;
+  static constexpr bool VISC = IsViscous<EQ>::value;
+  static constexpr int KINDS = NQ + 2;  // phase-A item kinds per line: Gauss points, two ends
+  // four warps per block and two blocks per SM: the derivative arithmetic
+  // needs up to 255 registers a thread, and two blocks with their own
+  // barriers let one block's stores overlap the other's arithmetic
+  static constexpr int THREADS = 128;
+  static constexpr int MINB = 2;
+  static constexpr int SZ11 = (NQ * NC * NC + 4 * NC * NC) * 32;
+  static constexpr int SZ12 = VISC ? (NQ * NC * NCD + 3 * NC * NCD) * 32 : 0;
+  static constexpr int SMEM = (SZ11 > SZ12 ? SZ11 : SZ12) * (int)sizeof(R) + 32 * (int)sizeof(int);
+  static constexpr int64_t NK11 = (N * N + 2 * N) * NC * NC;
+  static constexpr int64_t NK12 = VISC ? (N * N + N) * NC * NCD : 1;
+  static constexpr int OFF11 = N * N * NC * NC;
+  static constexpr int OFF12 = N * N * NC * NCD;
+};
+
+// line L -> (element, direction, first node, node stride)
+template <int D, int P>
+struct LineAt {
+  int64_t e;
+  int d, b0, st;
+  __device__ __forceinline__ LineAt(int64_t L) {
+    using S = Shape<D, P>;
+    e = L / (D * S::NL);
+    d = (int)((L / S::NL) % D);
+    const int l = (int)(L % S::NL);
+    st = S::stride(d);
+    b0 = S::base(d, l);
+  }
+};
+
+// d(F^.n)/du at one line end, seeded on the inside (SIDE 0) or outside
+// (SIDE 1) trace: the interior, Neumann, no-slip wall and Dirichlet fluxes of
+// the residual (Eqs. 25-30, the wall flux of the builder's wall reading)
+template <int D, int NC, int EQ, typename R, int SIDE>
+__device__ __forceinline__ void end_flux_derivative(const R* uin, const R* uo, const R* qin, const R* qo,
+                                                    const R* nv, R nn, int nb, int swv, bool wall, bool neu,
+                                                    const Phys<R>& pp, R* out /* [NC][NC] */) {
+  using T = Dual<R, NC>;
+  constexpr bool VISC = IsViscous<EQ>::value;
+  constexpr int NCD = NC * D;
+  T ui[NC], ux[NC], F[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    ui[c] = SIDE == 0 ? dseed<R, NC>(uin[c], c) : dconst<R, NC>(uin[c]);
+    ux[c] = SIDE == 1 ? dseed<R, NC>(uo[c], c) : dconst<R, NC>(uo[c]);
+    F[c] = dconst<R, NC>(R(0));
+  }
+  if (nb >= 0) {
+    inviscid_numflux<EQ, D, T, R>(ux, ui, nv, pp, F);
+    if constexpr (VISC) {
+      T qq[NCD], fv[NC];
+      const bool from_out = swv == 1;
+#pragma unroll
+      for (int cb = 0; cb < NCD; ++cb) qq[cb] = dconst<R, NC>(from_out ? qo[cb] : qin[cb]);
+      if (from_out)
+        viscous_flux_n<EQ, D, T, R>(ux, qq, nv, pp, fv);
+      else
+        viscous_flux_n<EQ, D, T, R>(ui, qq, nv, pp, fv);
+      const R pen = pp.C11;  // per unit reference length
+#pragma unroll
+      for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
+    }
+  } else if (neu || SIDE == 1) {
+    // Neumann: the prescribed flux does not depend on the state; walls and
+    // Dirichlet data have no outside trace
+  } else if (wall) {
+    if constexpr (NC == D + 2) {
+      T m2 = ui[1] * ui[1];
+#pragma unroll
+      for (int a = 1; a < D; ++a) m2 = m2 + ui[1 + a] * ui[1 + a];
+      const T pr = (pp.gamma - R(1)) * (ui[D + 1] - R(0.5) * m2 / ui[0]);
+#pragma unroll
+      for (int a = 0; a < D; ++a) F[1 + a] = pr * nv[a];
+      if constexpr (VISC) {
+        T ub[NC], qq[NCD], fv[NC];
+        wall_state<D, T, R>(ui, ub);
+#pragma unroll
+        for (int cb = 0; cb < NCD; ++cb) qq[cb] = dconst<R, NC>(qin[cb]);
+        viscous_flux_n<EQ, D, T, R>(ub, qq, nv, pp, fv);
+        const R pen = pp.C11b * nn;
+#pragma unroll
+        for (int a = 0; a < D; ++a) F[1 + a] = F[1 + a] + fv[1 + a] + pen * (ui[1 + a] - ub[1 + a]);
+      }
+    }
+  } else {
+    // Dirichlet data g_D as the outside trace (constant)
+    inviscid_numflux<EQ, D, T, R>(ux, ui, nv, pp, F);
+    if constexpr (VISC) {
+      T qq[NCD], fv[NC];
+#pragma unroll
+      for (int cb = 0; cb < NCD; ++cb) qq[cb] = dconst<R, NC>(qin[cb]);
+      viscous_flux_n<EQ, D, T, R>(ui, qq, nv, pp, fv);
+      const R pen = pp.C11b * nn;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int cp = 0; cp < NC; ++cp) out[c * NC + cp] = F[c].d[cp];
+}
+
+template <int D, int P, int NC, int EQ, typename R>
+__global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::THREADS, (JacTile<D, P, NC, EQ, R>::MINB))
+    k_jacobian(const R* __restrict__ Ur, const R* __restrict__ Qr, R* __restrict__ K11, R* __restrict__ K12,
+               R* __restrict__ Kw, Geo g, Tab tab, PhysArgs ph, int64_t nlines) {
+  using JT = JacTile<D, P, NC, EQ, R>;
+  using S = Shape<D, P>;
+  constexpr int N = JT::N, NQ = JT::NQ, NPE = JT::NPE, NCD = JT::NCD;
+  constexpr bool VISC = JT::VISC;
+  extern __shared__ unsigned char smraw[];
+  R* const sm = reinterpret_cast<R*>(smraw);
+  int* const fend = reinterpret_cast<int*>(smraw + (JT::SMEM - 32 * (int)sizeof(int)));
   Phys<R> pp;
   pp.set(ph);
-  R ij[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) ij[i] = (R)g.invJ[e * NPE + b0 + i * st];
-  // end data
-  int32_t nb[2];
-  int swv[2];
-  bool wall[2], neu[2];
-  R nv[2][D], nn[2], uin[2][NC], uo[2][NC];
-  R qin[2][VISC ? NCD : 1], qo[2][VISC ? NCD : 1];
-#pragma unroll
-  for (int end = 0; end < 2; ++end) {
-    const int aend = b0 + end * P * st;
-    nb[end] = g.nbr[L * 2 + end];
-    swv[end] = g.sw[(e * D + d) * 2 + end];
-    wall[end] = nb[end] < 0 && ph.bck[-1 - nb[end]] == BC_WALL;
-    neu[end] = nb[end] < 0 && ph.bck[-1 - nb[end]] == BC_NEUMANN;
-    R s = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      nv[end][a] = (R)g.nend[(L * 2 + end) * D + a];
-      s += nv[end][a] * nv[end][a];
-    }
-    nn[end] = sqrt(s);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) uin[end][c] = uel[c * NPE + aend];
-    if constexpr (VISC) {
-#pragma unroll
-      for (int cb = 0; cb < NCD; ++cb) qin[end][cb] = qel[cb * NPE + aend];
-    }
-    if (nb[end] >= 0) {
-      const int64_t eo = nb[end] / NPE;
-      const int ao = nb[end] % NPE;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) uo[end][c] = (R)U[eo * tile + c * NPE + ao];
-      if constexpr (VISC) {
-#pragma unroll
-        for (int cb = 0; cb < NCD; ++cb) qo[end][cb] = (R)Q[(eo * NCD + cb) * NPE + ao];
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) uo[end][c] = g.gD ? (R)g.gD[e * tile + c * NPE + aend] : R(0);
-      if constexpr (VISC) {
-#pragma unroll
-        for (int cb = 0; cb < NCD; ++cb) qo[end][cb] = R(0);
-      }
-    }
-  }
+  const int64_t tile0 = (int64_t)blockIdx.x * 32;
 
-  // the gradient's trace at a no-slip wall is the wall state of the inside
-  // trace: its derivative is the identity on rho, zero on momentum, and the
-  // energy row w = (|m|^2 / (2 rho^2), -m / rho, 1); w is stored per line end
-  // (zero at other ends) for the K21 part of the split product
-  if constexpr (VISC && NC == D + 2) {
-    if (Kw) {
-#pragma unroll
-      for (int end = 0; end < 2; ++end) {
-        R w[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) w[c] = R(0);
-        if (wall[end]) {
-          const R rho = uin[end][0];
-          R m2 = R(0);
-#pragma unroll
-          for (int a = 0; a < D; ++a) m2 += uin[end][1 + a] * uin[end][1 + a];
-          w[0] = m2 / (R(2) * rho * rho);
-#pragma unroll
-          for (int a = 0; a < D; ++a) w[1 + a] = -uin[end][1 + a] / rho;
-          w[NC - 1] = R(1);
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) Kw[tile_index(L, 2 * NC, end * NC + c)] = w[c];
-      }
-    }
-  }
-
-  // ---------------- K11: one column (component cp of u) at a time ---------
-#pragma unroll 1
-  for (int cp = 0; cp < NC; ++cp) {
-    R acc[N][N][NC];
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-      for (int j = 0; j < N; ++j)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[i][j][c] = R(0);
-#pragma unroll 1
-    for (int q = 0; q < NQ; ++q) {
+  // ======================= K11 round =======================================
+  R* A = sm;                         // [NQ][NC][NC][32]
+  R* B = sm + NQ * NC * NC * 32;     // [end][side][NC][NC][32]
+  for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::THREADS) {
+    const int lane = it & 31, kind = it >> 5;
+    const int64_t L = tile0 + lane;
+    if (L >= nlines) continue;
+    const LineAt<D, P> ln(L);
+    const R* ue = Ur + ln.e * NC * NPE;
+    if (kind < NQ) {
+      const int q = kind;
       R n[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) n[a] = sN[(q * D + a) * S::THREADS + threadIdx.x];
-      T uq[NC];
+      for (int a = 0; a < D; ++a) n[a] = (R)g.ng[(L * NQ + q) * D + a];
+      using T = Dual<R, NC>;
+      T uq[NC], f[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         R s = 0;
 #pragma unroll
-        for (int t = 0; t < N; ++t) s += tphi<R>(tab, q, t) * uel[c * NPE + b0 + t * st];
-        uq[c] = D1<R>::seed(s, c == cp);
+        for (int t = 0; t < N; ++t) s += tphi<R>(tab, q, t) * ue[c * NPE + ln.b0 + t * ln.st];
+        uq[c] = dseed<R, NC>(s, c);
       }
-      T f[NC];
       inviscid_flux_n<EQ, D, T, R>(uq, n, pp, f);
       if constexpr (VISC) {
+        const R* qe = Qr + ln.e * NCD * NPE;
         T qq[NCD], fv[NC];
 #pragma unroll
         for (int cb = 0; cb < NCD; ++cb) {
           R s = 0;
 #pragma unroll
-          for (int t = 0; t < N; ++t) s += tphi<R>(tab, q, t) * qel[cb * NPE + b0 + t * st];
-          qq[cb] = D1<R>::cst(s);
+          for (int t = 0; t < N; ++t) s += tphi<R>(tab, q, t) * qe[cb * NPE + ln.b0 + t * ln.st];
+          qq[cb] = dconst<R, NC>(s);
         }
         viscous_flux_n<EQ, D, T, R>(uq, qq, n, pp, fv);
 #pragma unroll
         for (int c = 0; c < NC; ++c) f[c] = f[c] + fv[c];
       }
 #pragma unroll
-      for (int i = 0; i < N; ++i)
+      for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const R w = kdphi<R>(tab, i, q, j);
+        for (int cp = 0; cp < NC; ++cp) A[((q * NC + c) * NC + cp) * 32 + lane] = f[c].d[cp];
+    } else {
+      const int end = kind - NQ;
+      const int aend = ln.b0 + end * P * ln.st;
+      const int nb = g.nbr[L * 2 + end];
+      const int swv = g.sw[(ln.e * D + ln.d) * 2 + end];
+      const bool wall = nb < 0 && ph.bck[-1 - nb] == BC_WALL;
+      const bool neu = nb < 0 && ph.bck[-1 - nb] == BC_NEUMANN;
+      R nv[D], nn = 0;
 #pragma unroll
-          for (int c = 0; c < NC; ++c) acc[i][j][c] -= w * f[c].d[0];
+      for (int a = 0; a < D; ++a) {
+        nv[a] = (R)g.nend[(L * 2 + end) * D + a];
+        nn += nv[a] * nv[a];
+      }
+      nn = sqrt(nn);
+      R uin[NC], uo[NC], qin[VISC ? NCD : 1], qo[VISC ? NCD : 1];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) uin[c] = ue[c * NPE + aend];
+      if constexpr (VISC) {
+#pragma unroll
+        for (int cb = 0; cb < NCD; ++cb) qin[cb] = Qr[(ln.e * NCD + cb) * NPE + aend];
+      }
+      if (nb >= 0) {
+        const int64_t eo = nb / NPE;
+        const int ao = nb % NPE;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) uo[c] = Ur[(eo * NC + c) * NPE + ao];
+        if constexpr (VISC) {
+#pragma unroll
+          for (int cb = 0; cb < NCD; ++cb) qo[cb] = Qr[(eo * NCD + cb) * NPE + ao];
         }
-    }
+      } else {
 #pragma unroll
-    for (int end = 0; end < 2; ++end) {
-      const int jn = end * P;
-      // derivative w.r.t. the inside trace (column of the in-line block at jn)
-      // and w.r.t. the outside trace (face block)
-#pragma unroll 1
-      for (int side = 0; side < 2; ++side) {
-        T ui[NC], ux[NC], F[NC];
+        for (int c = 0; c < NC; ++c) uo[c] = g.gD ? (R)g.gD[(ln.e * NC + c) * NPE + aend] : R(0);
+        if constexpr (VISC) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          ui[c] = D1<R>::seed(uin[end][c], side == 0 && c == cp);
-          ux[c] = D1<R>::seed(uo[end][c], side == 1 && c == cp);
-        }
-        if (nb[end] >= 0) {
-          inviscid_numflux<EQ, D, T, R>(ux, ui, nv[end], pp, F);
-          if constexpr (VISC) {
-            T qq[NCD], fv[NC];
-            if (swv[end] == 1) {
-#pragma unroll
-              for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qo[end][cb]);
-              viscous_flux_n<EQ, D, T, R>(ux, qq, nv[end], pp, fv);
-            } else {
-#pragma unroll
-              for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
-              viscous_flux_n<EQ, D, T, R>(ui, qq, nv[end], pp, fv);
-            }
-            const R pen = pp.C11 * nn[end];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
-          }
-        } else if (neu[end]) {
-          // Neumann: the prescribed flux does not depend on the state
-#pragma unroll
-          for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
-        } else if (wall[end]) {
-          // no-slip adiabatic wall: pressure flux, viscous momentum flux of
-          // the wall state, momentum penalty; no outside trace
-          if (side == 1) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
-          } else if constexpr (NC != D + 2) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
-          } else {
-            T m2 = ui[1] * ui[1];
-#pragma unroll
-            for (int a = 1; a < D; ++a) m2 = m2 + ui[1 + a] * ui[1 + a];
-            const T pr = (pp.gamma - R(1)) * (ui[D + 1] - R(0.5) * m2 / ui[0]);
-            F[0] = D1<R>::cst(R(0));
-#pragma unroll
-            for (int a = 0; a < D; ++a) F[1 + a] = pr * nv[end][a];
-            F[D + 1] = D1<R>::cst(R(0));
-            if constexpr (VISC) {
-              T ub[NC], qq[NCD], fv[NC];
-              wall_state<D, T, R>(ui, ub);
-#pragma unroll
-              for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
-              viscous_flux_n<EQ, D, T, R>(ub, qq, nv[end], pp, fv);
-              const R pen = pp.C11b * nn[end];
-#pragma unroll
-              for (int a = 0; a < D; ++a) F[1 + a] = F[1 + a] + fv[1 + a] + pen * (ui[1 + a] - ub[1 + a]);
-            }
-          }
-        } else {
-          // Dirichlet data: the outside trace is g_D, constant
-          if (side == 1) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) F[c] = D1<R>::cst(R(0));
-          } else {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) ux[c] = D1<R>::cst(uo[end][c]);
-            inviscid_numflux<EQ, D, T, R>(ux, ui, nv[end], pp, F);
-            if constexpr (VISC) {
-              T qq[NCD], fv[NC];
-#pragma unroll
-              for (int cb = 0; cb < NCD; ++cb) qq[cb] = D1<R>::cst(qin[end][cb]);
-              viscous_flux_n<EQ, D, T, R>(ui, qq, nv[end], pp, fv);
-              const R pen = pp.C11b * nn[end];
-#pragma unroll
-              for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
-            }
-          }
-        }
-        if (side == 0) {
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const R li = tlift<R>(tab, end, i);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) acc[i][jn][c] += li * F[c].d[0];
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const R li = tlift<R>(tab, end, i);
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-              K11[tile_index(L, NK11, OFF11 + ((end * N + i) * NC + c) * NC + cp)] = -ij[i] * li * F[c].d[0];
-          }
+          for (int cb = 0; cb < NCD; ++cb) qo[cb] = R(0);
         }
       }
+      // the gradient's trace at a no-slip wall is the wall state of the
+      // inside trace: identity on rho, zero on momentum and the energy row
+      // w = (|m|^2 / (2 rho^2), -m / rho, 1), stored per line end for the
+      // K21 part of the split product
+      if constexpr (VISC && NC == D + 2) {
+        if (Kw) {
+          R w[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) w[c] = R(0);
+          if (wall) {
+            const R rho = uin[0];
+            R m2 = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) m2 += uin[1 + a] * uin[1 + a];
+            w[0] = m2 / (R(2) * rho * rho);
+#pragma unroll
+            for (int a = 0; a < D; ++a) w[1 + a] = -uin[1 + a] / rho;
+            w[NC - 1] = R(1);
+          }
+#pragma unroll
+          for (int c = 0; c < NC; ++c) Kw[tile_index(L, 2 * NC, end * NC + c)] = w[c];
+        }
+      }
+      R dF[NC * NC];
+      end_flux_derivative<D, NC, EQ, R, 0>(uin, uo, qin, qo, nv, nn, nb, swv, wall, neu, pp, dF);
+#pragma unroll
+      for (int k = 0; k < NC * NC; ++k) B[((end * 2 + 0) * NC * NC + k) * 32 + lane] = dF[k];
+      end_flux_derivative<D, NC, EQ, R, 1>(uin, uo, qin, qo, nv, nn, nb, swv, wall, neu, pp, dF);
+#pragma unroll
+      for (int k = 0; k < NC * NC; ++k) B[((end * 2 + 1) * NC * NC + k) * 32 + lane] = dF[k];
     }
+  }
+  __syncthreads();
+  // phase B: row i, block column jj (in-line j < N, face blocks N, N + 1)
+  for (int it = threadIdx.x; it < 32 * N * (N + 2); it += JT::THREADS) {
+    const int lane = it & 31, r = it >> 5;
+    const int i = r / (N + 2), jj = r % (N + 2);
+    const int64_t L = tile0 + lane;
+    if (L >= nlines) continue;
+    const LineAt<D, P> ln(L);
+    const R ij = (R)g.invJ[ln.e * NPE + ln.b0 + i * ln.st];
+    if (jj < N) {
+      const int j = jj;
+      R w[NQ];
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+      for (int q = 0; q < NQ; ++q) w[q] = kdphi<R>(tab, i, q, j);
+      const R l0 = (j == 0) ? tlift<R>(tab, 0, i) : R(0);
+      const R l1 = (j == P) ? tlift<R>(tab, 1, i) : R(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j)
+      for (int k = 0; k < NC * NC; ++k) {
+        R s = l0 * B[((0 * 2 + 0) * NC * NC + k) * 32 + lane] + l1 * B[((1 * 2 + 0) * NC * NC + k) * 32 + lane];
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          K11[tile_index(L, NK11, ((i * N + j) * NC + c) * NC + cp)] = -ij[i] * acc[i][j][c];
+        for (int q = 0; q < NQ; ++q) s -= w[q] * A[(q * NC * NC + k) * 32 + lane];
+        K11[tile_index(L, JT::NK11, (i * N + j) * NC * NC + k)] = -ij * s;
+      }
+    } else {
+      const int end = jj - N;
+      const R li = tlift<R>(tab, end, i);
+#pragma unroll
+      for (int k = 0; k < NC * NC; ++k)
+        K11[tile_index(L, JT::NK11, JT::OFF11 + (end * N + i) * NC * NC + k)] =
+            -ij * li * B[((end * 2 + 1) * NC * NC + k) * 32 + lane];
+    }
   }
 
-  // ---------------- K12: the viscous flux is linear in q -----------------
+  // ======================= K12 round: F^vis is linear in q ================
   if constexpr (VISC) {
-#pragma unroll 1
-    for (int cb = 0; cb < NCD; ++cb) {
-      R unit[NCD];
+    __syncthreads();
+    R* A2 = sm;                            // [NQ][NC][NCD][32]
+    R* C2 = sm + NQ * NC * NCD * 32;       // [end][NC][NCD][32] in-line end terms
+    R* Cf = C2 + 2 * NC * NCD * 32;        // [NC][NCD][32] face block
+    for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::THREADS) {
+      const int lane = it & 31, kind = it >> 5;
+      const int64_t L = tile0 + lane;
+      if (L >= nlines) continue;
+      const LineAt<D, P> ln(L);
+      const R* ue = Ur + ln.e * NC * NPE;
+      if (kind < NQ) {
+        const int q = kind;
+        R n[D], uq[NC];
 #pragma unroll
-      for (int k = 0; k < NCD; ++k) unit[k] = (k == cb) ? R(1) : R(0);
-      R acc[N][N][NC];
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) acc[i][j][c] = R(0);
-#pragma unroll 1
-      for (int q = 0; q < NQ; ++q) {
-        R n[D], uq[NC], fv[NC];
-#pragma unroll
-        for (int a = 0; a < D; ++a) n[a] = sN[(q * D + a) * S::THREADS + threadIdx.x];
+        for (int a = 0; a < D; ++a) n[a] = (R)g.ng[(L * NQ + q) * D + a];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           R s = 0;
 #pragma unroll
-          for (int t = 0; t < N; ++t) s += tphi<R>(tab, q, t) * uel[c * NPE + b0 + t * st];
+          for (int t = 0; t < N; ++t) s += tphi<R>(tab, q, t) * ue[c * NPE + ln.b0 + t * ln.st];
           uq[c] = s;
         }
-        viscous_flux_n<EQ, D, R, R>(uq, unit, n, pp, fv);
+#pragma unroll 1
+        for (int cb = 0; cb < NCD; ++cb) {
+          R unit[NCD], fv[NC];
 #pragma unroll
-        for (int i = 0; i < N; ++i)
+          for (int k = 0; k < NCD; ++k) unit[k] = (k == cb) ? R(1) : R(0);
+          viscous_flux_n<EQ, D, R, R>(uq, unit, n, pp, fv);
 #pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const R w = kdphi<R>(tab, i, q, j);
+          for (int c = 0; c < NC; ++c) A2[((q * NC + c) * NCD + cb) * 32 + lane] = fv[c];
+        }
+      } else {
+        const int end = kind - NQ;
+        const int aend = ln.b0 + end * P * ln.st;
+        const int nb = g.nbr[L * 2 + end];
+        const int swv = g.sw[(ln.e * D + ln.d) * 2 + end];
+        const bool wall = nb < 0 && ph.bck[-1 - nb] == BC_WALL;
+        const bool neu = nb < 0 && ph.bck[-1 - nb] == BC_NEUMANN;
+        const bool outside = nb >= 0 && swv == 1;
+        R nv[D], ut[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[i][j][c] -= w * fv[c];
-          }
-      }
+        for (int a = 0; a < D; ++a) nv[a] = (R)g.nend[(L * 2 + end) * D + a];
+        if (outside) {
+          const int64_t eo = nb / NPE;
+          const int ao = nb % NPE;
 #pragma unroll
-      for (int end = 0; end < 2; ++end) {
-        const int jn = end * P;
-        const bool outside = nb[end] >= 0 && swv[end] == 1;
-        R fv[NC];
+          for (int c = 0; c < NC; ++c) ut[c] = Ur[(eo * NC + c) * NPE + ao];
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ut[c] = ue[c * NPE + aend];
+        }
         bool walled = false;
         if constexpr (NC == D + 2) {
-          if (wall[end]) {
+          if (wall) {
             // the wall's viscous flux: wall state, momentum components only
             R ub[NC];
-            wall_state<D, R, R>(uin[end], ub);
-            viscous_flux_n<EQ, D, R, R>(ub, unit, nv[end], pp, fv);
-            fv[0] = R(0);
-            fv[NC - 1] = R(0);
+            wall_state<D, R, R>(ut, ub);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ut[c] = ub[c];
             walled = true;
           }
         }
-        if (!walled) viscous_flux_n<EQ, D, R, R>(outside ? uo[end] : uin[end], unit, nv[end], pp, fv);
-        if (!outside && !neu[end]) {
+        if (swv == 1) fend[lane] = end;
+#pragma unroll 1
+        for (int cb = 0; cb < NCD; ++cb) {
+          R unit[NCD], fv[NC];
 #pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const R li = tlift<R>(tab, end, i);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) acc[i][jn][c] += li * fv[c];
+          for (int k = 0; k < NCD; ++k) unit[k] = (k == cb) ? R(1) : R(0);
+          viscous_flux_n<EQ, D, R, R>(ut, unit, nv, pp, fv);
+          if (walled) {
+            fv[0] = R(0);
+            fv[NC - 1] = R(0);
           }
-        }
-        if (swv[end] == 1) {  // the face block belongs to the S = +1 end
 #pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const R li = tlift<R>(tab, end, i);
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-              K12[tile_index(L, NK12, OFF12 + (i * NC + c) * NCD + cb)] =
-                  outside ? -ij[i] * li * fv[c] : R(0);
+          for (int c = 0; c < NC; ++c) {
+            C2[((end * NC + c) * NCD + cb) * 32 + lane] = (!outside && !neu) ? fv[c] : R(0);
+            if (swv == 1) Cf[(c * NCD + cb) * 32 + lane] = outside ? fv[c] : R(0);
           }
         }
       }
+    }
+    __syncthreads();
+    // phase B: row i, block column jj (in-line j < N, the face block N)
+    for (int it = threadIdx.x; it < 32 * N * (N + 1); it += JT::THREADS) {
+      const int lane = it & 31, r = it >> 5;
+      const int i = r / (N + 1), jj = r % (N + 1);
+      const int64_t L = tile0 + lane;
+      if (L >= nlines) continue;
+      const LineAt<D, P> ln(L);
+      const R ij = (R)g.invJ[ln.e * NPE + ln.b0 + i * ln.st];
+      if (jj < N) {
+        const int j = jj;
+        R w[NQ];
 #pragma unroll
-      for (int i = 0; i < N; ++i)
+        for (int q = 0; q < NQ; ++q) w[q] = kdphi<R>(tab, i, q, j);
+        const R l0 = (j == 0) ? tlift<R>(tab, 0, i) : R(0);
+        const R l1 = (j == P) ? tlift<R>(tab, 1, i) : R(0);
+#pragma unroll 5
+        for (int k = 0; k < NC * NCD; ++k) {
+          R s = l0 * C2[(0 * NC * NCD + k) * 32 + lane] + l1 * C2[(1 * NC * NCD + k) * 32 + lane];
 #pragma unroll
-        for (int j = 0; j < N; ++j)
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            K12[tile_index(L, NK12, ((i * N + j) * NC + c) * NCD + cb)] = -ij[i] * acc[i][j][c];
+          for (int q = 0; q < NQ; ++q) s -= w[q] * A2[(q * NC * NCD + k) * 32 + lane];
+          K12[tile_index(L, JT::NK12, (i * N + j) * NC * NCD + k)] = -ij * s;
+        }
+      } else {
+        const R li = tlift<R>(tab, fend[lane], i);
+#pragma unroll 5
+        for (int k = 0; k < NC * NCD; ++k)
+          K12[tile_index(L, JT::NK12, JT::OFF12 + i * NC * NCD + k)] = -ij * li * Cf[k * 32 + lane];
+      }
     }
   }
+}
+
+template <int D, int P, int EQ, typename R>
+cudaError_t run_jacobian(const ldg_handle* h, const R* Ur, const R* Qr, R* K11, R* K12, R* Kw, cudaStream_t st) {
+  constexpr int NC = NComp<EQ, D>::value;
+  using JT = JacTile<D, P, NC, EQ, R>;
+  auto kern = k_jacobian<D, P, NC, EQ, R>;
+  cudaError_t err = set_smem_once(kern, JT::SMEM);
+  if (err != cudaSuccess) return err;
+  // shared memory before L1: two blocks per SM need twice the tile buffers
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return err;
+  kern<<<(unsigned)h->ntiles(), JT::THREADS, JT::SMEM, st>>>(Ur, Qr, K11, K12, Kw, h->geo(), h->tab, h->phys,
+                                                             h->nlines());
+  count_launch();
+  return cudaGetLastError();
+}
+
+// FP32 copy of an FP64 array (the state and gradient of an FP32 Jacobian:
+// converted once, so the assembly spends no FP64 operations)
+static __global__ void k_to_float(float* __restrict__ out, const double* __restrict__ in, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
 }
 
 // K21 = dQ/dU, scalar and component-independent (Sec. 4.2), built in FP64:
@@ -476,23 +565,6 @@ __global__ void k_build_k21(R* __restrict__ K21, Geo g, Tab tab, PhysArgs ph, in
       K21[tile_index(L, NK, N * N * D + i * D + b)] = (R)(ij * s);
     }
   }
-}
-
-template <int D, int P, int EQ, typename R>
-cudaError_t run_jacobian(const ldg_handle* h, const double* U, const double* Q, R* K11, R* K12, R* Kw,
-                         cudaStream_t st) {
-  using S = Shape<D, P>;
-  constexpr int NC = NComp<EQ, D>::value;
-  constexpr bool VISC = IsViscous<EQ>::value;
-  const size_t smem = ((size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0)) +
-                       (size_t)S::THREADS * S::NQ * D) * sizeof(R);
-  auto kern = k_jacobian<D, P, NC, EQ, R>;
-  cudaError_t err = set_smem_once(kern, smem);
-  if (err != cudaSuccess) return err;
-  const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
-  kern<<<(unsigned)blocks, S::THREADS, smem, st>>>(U, Q, K11, K12, Kw, h->geo(), h->tab, h->phys);
-  count_launch();
-  return cudaGetLastError();
 }
 
 template <int D, int P, typename R>

@@ -75,6 +75,7 @@ extern "C" int ldg_jac_destroy(ldg_jac_t* J) {
   cudaFree(J->K21);
   cudaFree(J->Kw);
   cudaFree(J->gbuf);
+  cudaFree(J->ucvt);
   delete J;
   return LDG_OK;
 }
@@ -100,6 +101,8 @@ extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_
       if (err == cudaSuccess) err = cudaMalloc(&J->gbuf, (size_t)h->ndof * h->D * sizeof(double));
       if (err == cudaSuccess && h->has_wall) err = cudaMalloc(&J->Kw, rows * 2 * h->nc * esize(prec));
     }
+    if (err == cudaSuccess && prec == LDG_PREC_FP32)
+      err = cudaMalloc(&J->ucvt, (size_t)h->ndof * (h->viscous() ? 1 + h->D : 1) * sizeof(float));
     if (err != cudaSuccess) {
       ldg_jac_destroy(J);
       return LDG_ERR_CUDA;
@@ -150,7 +153,7 @@ extern "C" int ldg_jacvec(ldg_handle_t* h, const ldg_jac_t* J, double shift, dou
 extern "C" int ldg_pc_destroy(ldg_pc_t* P) {
   if (!P) return LDG_OK;
   cudaFree(P->F);
-  cudaFree(P->Dinv);
+  cudaFree(P->Udiag);
   delete P;
   return LDG_OK;
 }
@@ -167,7 +170,7 @@ extern "C" int ldg_precond(ldg_handle_t* h, const ldg_jac_t* J, double shift, do
     P->prec = J->prec;
     const size_t bb = (size_t)h->nc * h->nc;
     cudaError_t err = cudaMalloc(&P->F, (size_t)h->E * h->npe * h->pat_w() * bb * esize(J->prec));
-    if (err == cudaSuccess) err = cudaMalloc(&P->Dinv, (size_t)h->E * h->npe * bb * esize(J->prec));
+    if (err == cudaSuccess) err = cudaMalloc(&P->Udiag, (size_t)h->E * h->npe * bb * esize(J->prec));
     if (err != cudaSuccess) {
       ldg_pc_destroy(P);
       return LDG_ERR_CUDA;
@@ -191,6 +194,19 @@ extern "C" int ldg_pc_export(const ldg_pc_t* P, void* factors) {
   if (!P || !factors) return LDG_ERR_ARG;
   if (!P->built) return LDG_ERR_NOT_BUILT;
   const ldg_handle* h = P->h;
-  const size_t bytes = (size_t)h->E * h->npe * h->pat_w() * h->nc * h->nc * esize(P->prec);
-  return cudaMemcpy(factors, P->F, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
+  const size_t bb = (size_t)h->nc * h->nc, W = h->pat_w(), es = esize(P->prec);
+  const size_t bytes = (size_t)h->E * h->npe * W * bb * es;
+  if (cudaMemcpy(factors, P->F, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return LDG_ERR_CUDA;
+  // the device keeps D_i^-1 in each row's diagonal slot and U_ii aside:
+  // put U_ii back (the factors as ILU(0) defines them)
+  std::vector<char> ud((size_t)h->E * h->npe * bb * es);
+  if (cudaMemcpy(ud.data(), P->Udiag, ud.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return LDG_ERR_CUDA;
+  const int N = h->p + 1;
+  for (int64_t e = 0; e < h->E; ++e)
+    for (int i = 0; i < h->npe; ++i) {
+      const int dg = i % N + (i / N) % N + (h->D == 3 ? i / (N * N) : 0);  // slots of lower columns
+      std::memcpy((char*)factors + (((size_t)e * h->npe + i) * W + dg) * bb * es,
+                  ud.data() + ((size_t)e * h->npe + i) * bb * es, bb * es);
+    }
+  return LDG_OK;
 }

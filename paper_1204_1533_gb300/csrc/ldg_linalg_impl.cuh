@@ -301,12 +301,12 @@ struct PcTables {
 };
 
 // INPLACE: the element block is assembled and factored directly in its
-// slice of F / Dinv in global memory (L2-resident while the block works on
+// slice of F / Ud in global memory (L2-resident while the block works on
 // it) when it does not fit in shared memory (FP64 at 3-D, p = 4).
 template <int D, int P, int NC, bool VISC, typename R, bool INPLACE>
 __global__ void __launch_bounds__(256)
     k_precond(const R* __restrict__ K11, const R* __restrict__ K12, const R* __restrict__ K21,
-              const R* __restrict__ Kw, R* F, R* Dinv, Geo g, Tab tab, PcTables pt, double shift,
+              const R* __restrict__ Kw, R* F, R* Ud, Geo g, Tab tab, PcTables pt, double shift,
               double scale) {
   using S = Shape<D, P>;
   constexpr int N = S::N, NPE = S::NPE, NL = S::NL, W = D * P + 1, NCD = NC * D, BB = NC * NC;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256)
   extern __shared__ unsigned char smraw[];
   R* const sm = reinterpret_cast<R*>(smraw);
   R* A = INPLACE ? F + (int64_t)blockIdx.x * NPE * W * BB : sm + NPE * W * D;  // [NPE][W][NC][NC]
-  R* Di = INPLACE ? Dinv + (int64_t)blockIdx.x * NPE * BB : A + NPE * W * BB;   // [NPE][NC][NC]
+  R* Di = INPLACE ? Ud + (int64_t)blockIdx.x * NPE * BB : A + NPE * W * BB;   // [NPE][NC][NC] inverses
   R* K21e = sm;                                    // [NPE][W][D] element part of K21
   __shared__ int16_t pat_s[NPE * W];
   __shared__ int8_t slot_s[NPE * NPE];
@@ -514,9 +514,27 @@ __global__ void __launch_bounds__(256)
       __syncthreads();
     }
   }
+  // stored for the apply: each row's diagonal slot holds D_i^-1 (the only
+  // diagonal quantity the triangular solves use), so a row's factors are one
+  // contiguous run with no unread block between them; U_ii goes to Ud (read
+  // only by the export)
   if constexpr (!INPLACE) {
-    for (int k = tid; k < NPE * W * BB; k += nt) F[e * NPE * W * BB + k] = A[k];
-    for (int k = tid; k < NPE * BB; k += nt) Dinv[e * NPE * BB + k] = Di[k];
+    for (int k = tid; k < NPE * W * BB; k += nt) {
+      const int i = k / (W * BB), sl = (k / BB) % W;
+      F[e * NPE * W * BB + k] = (pat_s[i * W + sl] == i) ? Di[i * BB + k % BB] : A[k];
+    }
+    for (int k = tid; k < NPE * BB; k += nt) {
+      const int i = k / BB;
+      Ud[e * NPE * BB + k] = A[(i * W + slot_s[i * NPE + i]) * BB + k % BB];
+    }
+  } else {
+    for (int k = tid; k < NPE * BB; k += nt) {
+      const int i = k / BB;
+      R* a = A + (i * W + slot_s[i * NPE + i]) * BB + k % BB;
+      const R u = *a;
+      *a = Di[k];
+      Di[k] = u;
+    }
   }
 }
 
@@ -627,7 +645,7 @@ struct RowPos {
 
 template <int D, int P, int NC, int G, typename R, typename V>
 __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
-    k_precond_apply(const R* __restrict__ F, const R* __restrict__ Dinv, const V* __restrict__ r,
+    k_precond_apply(const R* __restrict__ F, const V* __restrict__ r,
                     V* __restrict__ z, int64_t E) {
   using A = ApplyLanes<D, P, NC, G, R, V>;
   constexpr int N = A::N, NPE = A::NPE, W = A::W, BB = A::BB, EPW = A::EPW, MPL = A::MPL;
@@ -646,7 +664,7 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
   if (act)
     for (int k = q; k < tile; k += A::LPE) y[k] = r[e * tile + k];
   const R* Fe = F + (act ? e : 0) * (int64_t)NPE * W * BB + c * NC + m0;
-  const R* De = Dinv + (act ? e : 0) * (int64_t)NPE * BB + c * NC + m0;
+
   R fb[PD + 1][MAXS][MPL];
   R db[PD + 1][MPL];
   // factors of task t: forward row t + 1 (lower slots) or backward row
@@ -659,7 +677,7 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
 #pragma unroll
       for (int k = 0; k < MAXS; ++k)
         if (k < ns) load_run<MPL>(Fe + (ps.i * W + s0 + k) * BB, fb[b][k]);
-      if (!fwd) load_run<MPL>(De + ps.i * BB, db[b]);
+      if (!fwd) load_run<MPL>(Fe + (ps.i * W + ps.dg) * BB, db[b]);  // D_i^-1 in the diagonal slot
     }
   };
 #pragma unroll
@@ -671,9 +689,10 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
     const bool fwd = t < NPE - 1;
     const Pos ps(fwd ? t + 1 : 2 * NPE - 2 - t);
     const int b = t % (PD + 1);
-    V acc[MPL];
-#pragma unroll
-    for (int mm = 0; mm < MPL; ++mm) acc[mm] = V(0);
+    // one chain per lane, started at -y_i on the lane that owns the row's
+    // value: the group sum is then -(y_i - sum F y) with no separate partial
+    // sums or subtraction (in FP64 every addition costs the narrow FP64 pipe)
+    V acc = (act && g == 0) ? -y[c * NPE + ps.i] : V(0);
     if (act) {
       if (fwd) {
 #pragma unroll
@@ -681,7 +700,7 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
           if (k < ps.dg) {
             const int col = ps.lower_col(k);
 #pragma unroll
-            for (int mm = 0; mm < MPL; ++mm) acc[mm] += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
+            for (int mm = 0; mm < MPL; ++mm) acc += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
           }
       } else {
 #pragma unroll
@@ -689,24 +708,21 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
           if (k < MAXS - ps.dg) {
             const int col = ps.upper_col(k);
 #pragma unroll
-            for (int mm = 0; mm < MPL; ++mm) acc[mm] += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
+            for (int mm = 0; mm < MPL; ++mm) acc += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
           }
       }
     }
-    V pv = 0;
-#pragma unroll
-    for (int mm = 0; mm < MPL; ++mm) pv += acc[mm];
-    const V s = group_sum<G>(pv, sc, lane);
+    const V ns = group_sum<G>(acc, sc, lane);  // -(y_i - sum)
     if (fwd) {
-      if (act && g == 0) y[c * NPE + ps.i] -= s;
+      if (act && g == 0) y[c * NPE + ps.i] = -ns;
       __syncwarp();
     } else {
-      if (act && g == 0) tbuf[c] = y[c * NPE + ps.i] - s;
+      if (act && g == 0) tbuf[c] = ns;
       __syncwarp();
       V d = 0;
       if (act) {
 #pragma unroll
-        for (int mm = 0; mm < MPL; ++mm) d += (V)db[b][mm] * tbuf[m0 + mm];
+        for (int mm = 0; mm < MPL; ++mm) d -= (V)db[b][mm] * tbuf[m0 + mm];
       }
       const V zi = group_sum<G>(d, sc, lane);
       if (act && g == 0) y[c * NPE + ps.i] = zi;
@@ -770,7 +786,7 @@ constexpr size_t precond_static_smem() {
 
 template <int D, int P, int EQ, typename R>
 cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R* K21, const R* Kw, R* F,
-                        R* Dinv, double shift, double scale, cudaStream_t st) {
+                        R* Ud, double shift, double scale, cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
   constexpr bool VISC = IsViscous<EQ>::value;
   constexpr int W = D * P + 1;
@@ -780,14 +796,14 @@ cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R
     auto kern = k_precond<D, P, NC, VISC, R, false>;
     err = set_smem_once(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, Kw, F, Dinv, h->geo(), h->tab, pc_tables(h), shift,
+    kern<<<(unsigned)h->E, 256, smem, st>>>(K11, K12, K21, Kw, F, Ud, h->geo(), h->tab, pc_tables(h), shift,
                                              scale);
   } else {
     const size_t sm_in = (size_t)Shape<D, P>::NPE * W * D * sizeof(R);
     auto kern = k_precond<D, P, NC, VISC, R, true>;
     err = set_smem_once(kern, sm_in);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)h->E, 256, sm_in, st>>>(K11, K12, K21, Kw, F, Dinv, h->geo(), h->tab, pc_tables(h), shift,
+    kern<<<(unsigned)h->E, 256, sm_in, st>>>(K11, K12, K21, Kw, F, Ud, h->geo(), h->tab, pc_tables(h), shift,
                                               scale);
   }
   count_launch();
@@ -795,17 +811,17 @@ cudaError_t run_precond(const ldg_handle* h, const R* K11, const R* K12, const R
 }
 
 template <int D, int P, int NC, int G, typename R, typename V>
-cudaError_t launch_apply_lanes(const ldg_handle* h, const R* F, const R* Dinv, const V* r, V* z, cudaStream_t st) {
+cudaError_t launch_apply_lanes(const ldg_handle* h, const R* F, const V* r, V* z, cudaStream_t st) {
   using A = ApplyLanes<D, P, NC, G, R, V>;
   const int64_t epb = (int64_t)A::EPW * A::WPB;
   const int64_t blocks = (h->E + epb - 1) / epb;
-  k_precond_apply<D, P, NC, G, R, V><<<(unsigned)blocks, A::THREADS, 0, st>>>(F, Dinv, r, z, h->E);
+  k_precond_apply<D, P, NC, G, R, V><<<(unsigned)blocks, A::THREADS, 0, st>>>(F, r, z, h->E);
   count_launch();
   return cudaGetLastError();
 }
 
 template <int D, int P, int EQ, typename R, typename V>
-cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const R* Dinv, const V* r, V* z,
+cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const V* r, V* z,
                               cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
   // FP32: one lane per block entry (the most parallelism). FP64: one lane
@@ -818,11 +834,11 @@ cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const R* Dinv, co
       const int64_t warps_g1 = (h->E + ApplyLanes<D, P, NC, 1, R, V>::EPW - 1) / ApplyLanes<D, P, NC, 1, R, V>::EPW;
       int dev = 0, sms = 152;
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (warps_g1 < 6 * (int64_t)sms) return launch_apply_lanes<D, P, NC, 2, R, V>(h, F, Dinv, r, z, st);
+      if (warps_g1 < 6 * (int64_t)sms) return launch_apply_lanes<D, P, NC, 2, R, V>(h, F, r, z, st);
     }
-    return launch_apply_lanes<D, P, NC, 1, R, V>(h, F, Dinv, r, z, st);
+    return launch_apply_lanes<D, P, NC, 1, R, V>(h, F, r, z, st);
   } else {
-    return launch_apply_lanes<D, P, NC, NC, R, V>(h, F, Dinv, r, z, st);
+    return launch_apply_lanes<D, P, NC, NC, R, V>(h, F, r, z, st);
   }
 }
 

@@ -28,7 +28,20 @@ template <int D, int EQ>
 cudaError_t Ops<D, EQ>::jacobian(const ldg_handle* h, const double* U, const double* Q, ldg_jac* J,
                                  cudaStream_t st) {
   if (J->prec == LDG_PREC_FP32) {
-#define F(P) return run_jacobian<D, P, EQ, float>(h, U, Q, (float*)J->K11, (float*)J->K12, (float*)J->Kw, st)
+    // FP32 copies of U (and Q): one conversion per value instead of one per use
+    float* uf = (float*)J->ucvt;
+    float* qf = h->viscous() ? uf + h->ndof : nullptr;
+    const int64_t nconv = h->ndof * (h->viscous() ? 1 + h->D : 1);
+    if (!uf) return cudaErrorInvalidValue;
+    k_to_float<<<(unsigned)((h->ndof + 255) / 256 < 4096 ? (h->ndof + 255) / 256 : 4096), 256, 0, st>>>(uf, U,
+                                                                                                    h->ndof);
+    count_launch();
+    if (qf) {
+      k_to_float<<<(unsigned)((nconv - h->ndof + 255) / 256 < 4096 ? (nconv - h->ndof + 255) / 256 : 4096), 256, 0,
+                   st>>>(qf, Q, nconv - h->ndof);
+      count_launch();
+    }
+#define F(P) return run_jacobian<D, P, EQ, float>(h, uf, qf, (float*)J->K11, (float*)J->K12, (float*)J->Kw, st)
     LDG_FOR_P(F)
 #undef F
   } else {
@@ -89,14 +102,14 @@ cudaError_t Ops<D, EQ>::precond(const ldg_handle* h, const ldg_jac* J, double sh
 #define F(PP)                                                                                   \
   return run_precond<D, PP, EQ, float>(h, (const float*)J->K11, (const float*)J->K12,           \
                                        (const float*)J->K21, (const float*)J->Kw, (float*)P->F,    \
-                                       (float*)P->Dinv, shift, scale, st)
+                                       (float*)P->Udiag, shift, scale, st)
     LDG_FOR_P(F)
 #undef F
   } else {
 #define F(PP)                                                                                       \
   return run_precond<D, PP, EQ, double>(h, (const double*)J->K11, (const double*)J->K12,            \
                                         (const double*)J->K21, (const double*)J->Kw, (double*)P->F,    \
-                                        (double*)P->Dinv, shift, scale, st)
+                                        (double*)P->Udiag, shift, scale, st)
     LDG_FOR_P(F)
 #undef F
   }
@@ -108,13 +121,13 @@ cudaError_t Ops<D, EQ>::apply(const ldg_handle* h, const ldg_pc* P, const void* 
                               cudaStream_t st) {
   if (P->prec == LDG_PREC_FP32 && vprec == LDG_PREC_FP32) {
 #define F(PP)                                                                                     \
-  return run_precond_apply<D, PP, EQ, float, float>(h, (const float*)P->F, (const float*)P->Dinv, \
+  return run_precond_apply<D, PP, EQ, float, float>(h, (const float*)P->F, \
                                                     (const float*)r, (float*)z, st)
     LDG_FOR_P(F)
 #undef F
   } else if (P->prec == LDG_PREC_FP64 && vprec == LDG_PREC_FP64) {
 #define F(PP)                                                                                        \
-  return run_precond_apply<D, PP, EQ, double, double>(h, (const double*)P->F, (const double*)P->Dinv, \
+  return run_precond_apply<D, PP, EQ, double, double>(h, (const double*)P->F, \
                                                       (const double*)r, (double*)z, st)
     LDG_FOR_P(F)
 #undef F

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(Shape<D, P>::THREADS)
           } else {
             viscous_flux_n<EQ, D, double, double>(uin, qin, nv, pp, fv);
           }
-          const double pen = ph.C11 * nn;
+          const double pen = ph.C11;  // per unit reference length: C11 / h physically
 #pragma unroll
           for (int c = 0; c < NC; ++c) F[c] += fv[c] + pen * (uin[c] - uout[c]);
         }

@@ -412,6 +412,10 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
       k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(w.r64, w.G, -1.0, n);
       count_launch();
       const int sweeps = o->max_refine < 1 ? 1 : o->max_refine;
+      // relative tolerance of this linear solve: gmres_tol, or with the
+      // target-aware forcing no more than the stopping rule still needs
+      double eta = o->gmres_tol;
+      if (o->forcing == LDG_FORCING_TARGET && gn > 0.0) eta = std::fmin(0.5, std::fmax(eta, 0.5 * target / gn));
       for (int s = 0; s < sweeps; ++s) {
         if (s > 0) {
           if (launch_jacvec(h, h->Jn, 1.0, -adt, w.delta, w.tmp64, LDG_PREC_FP64, st) != cudaSuccess)
@@ -424,9 +428,9 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
         double rn = 0;
         rc = norm2(h, w.r64, &rn, w, st);
         if (rc) return rc;
-        if (rn <= o->gmres_tol * gn || rn == 0.0) break;
-        // relative tolerance of this cycle so that it reaches gmres_tol ||G||
-        const double tol = o->gmres_tol * gn / rn;
+        if (rn <= eta * gn || rn == 0.0) break;
+        // relative tolerance of this cycle so that it reaches eta ||G||
+        const double tol = eta * gn / rn;
         int its = 0;
         double rel = 0;
         if (mode == LDG_MODE_FP64) {

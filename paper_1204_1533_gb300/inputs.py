@@ -524,6 +524,35 @@ def channel_state(mesh, gamma=1.4, mach=0.3, amp=0.01, seed=STATE_SEED):
     return _to_conserved(rho, [u, v, w], p, gamma)
 
 
+def poisson_mapped_square_mesh(n=8, p=3, amp=0.08):
+    """Unit square, n x n quads whose nodes are moved by the smooth map
+    (x + amp sin(pi x) sin(2 pi y), y + amp sin(2 pi x) sin(pi y)): curved
+    isoparametric elements that stay nested under refinement (every n
+    samples the same map, unlike a per-level random perturbation); the map
+    keeps each side of the square on itself. All sides Dirichlet (tag 0)."""
+    m = structured_mesh((n, n), p, (0.0, 0.0), (1.0, 1.0), (False, False), perturb=0.0)
+    X, Y = m["nodes"][..., 0].copy(), m["nodes"][..., 1].copy()
+    m["nodes"][..., 0] = X + amp * np.sin(math.pi * X) * np.sin(2.0 * math.pi * Y)
+    m["nodes"][..., 1] = Y + amp * np.sin(2.0 * math.pi * X) * np.sin(math.pi * Y)
+    return m
+
+
+def poisson_paper_solution(mesh, alpha=0.1, beta=0.3, a=5.1, b=-6.2, c=4.3, d=3.4):
+    """The manufactured solution of the paper's Poisson study (Sec. 5.1, its
+    printed constants): u = exp(alpha sin(a x + b y) + beta cos(c x + d y)),
+    with its gradient and f = -lap u at the nodes. Returns (u [E, 1, npe],
+    grad u [E, 1, 2, npe], f [E, 1, npe]); u is also the Dirichlet data."""
+    x, y = mesh["nodes"][..., 0], mesh["nodes"][..., 1]
+    s1, c1 = np.sin(a * x + b * y), np.cos(a * x + b * y)
+    s2, c2 = np.sin(c * x + d * y), np.cos(c * x + d * y)
+    u = np.exp(alpha * s1 + beta * c2)
+    px = alpha * a * c1 - beta * c * s2
+    py = alpha * b * c1 - beta * d * s2
+    lap_phi = -alpha * (a * a + b * b) * s1 - beta * (c * c + d * d) * c2
+    f = -u * (px * px + py * py + lap_phi)
+    return u[:, None], np.stack([u * px, u * py], axis=1)[:, None], f[:, None]
+
+
 def poisson_exact(mesh):
     """Manufactured u = sin(pi x) sin(pi y), [E, 1, (p+1)^2]."""
     x, y = mesh["nodes"][..., 0], mesh["nodes"][..., 1]

@@ -50,7 +50,8 @@ class ldg_solver_opts_t(C.Structure):
     _fields_ = [("mode", C.c_int32), ("predictor", C.c_int32), ("first_step", C.c_int32),
                 ("restart", C.c_int32), ("max_newton", C.c_int32), ("reuse", C.c_int32),
                 ("max_refine", C.c_int32), ("force_rebuild", C.c_int32),
-                ("rtol", C.c_double), ("gmres_tol", C.c_double), ("stall_rebuild", C.c_int32)]
+                ("rtol", C.c_double), ("gmres_tol", C.c_double), ("stall_rebuild", C.c_int32),
+                ("forcing", C.c_int32)]
 
 
 class ldg_step_stats_t(C.Structure):
@@ -383,11 +384,14 @@ def ldg_pc_export(P, prec):
     return F
 
 
+FORCING_FIXED, FORCING_TARGET = 0, 1
+
+
 def solver_opts(mode=MODE_MIXED, predictor=PRED_EXTRAP, first_step=False, restart=30,
                 max_newton=50, reuse=15, max_refine=10, force_rebuild=True, rtol=1e-8,
-                gmres_tol=1e-3, stall_rebuild=True):
+                gmres_tol=1e-3, stall_rebuild=True, forcing=FORCING_FIXED):
     return ldg_solver_opts_t(mode, predictor, int(first_step), restart, max_newton, reuse,
-                             max_refine, int(force_rebuild), rtol, gmres_tol, int(stall_rebuild))
+                             max_refine, int(force_rebuild), rtol, gmres_tol, int(stall_rebuild), int(forcing))
 
 
 def ldg_newton_step(h, U_next, U_n, U_nm1, U_nm2, dt, opts, stream=None):

@@ -34,12 +34,13 @@ def tgv_problem(n, p=3, re=1600.0):
     return m, dict(NS, mu=1.0 / re), I.tgv_state(m)
 
 
-def _step(h, Un, Unm1, dt, first, mode, predictor=ldg.PRED_EXTRAP, guess=None, force=False):
+def _step(h, Un, Unm1, dt, first, mode, predictor=ldg.PRED_EXTRAP, guess=None, force=False,
+          forcing=ldg.FORCING_FIXED):
     import torch
     Unext = torch.empty_like(Un) if guess is None else guess
     st = ldg.ldg_newton_step(h, Unext, Un, Unm1, None, dt,
                              ldg.solver_opts(mode=mode, predictor=predictor, first_step=first,
-                                             force_rebuild=force))
+                                             force_rebuild=force, forcing=forcing))
     return Unext, st
 
 
@@ -125,11 +126,12 @@ def _timed(fn):
     return out, (time.perf_counter() - t0) * 1e3
 
 
-def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
+def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True, forcing=ldg.FORCING_FIXED):
     """Solve the held-out trajectory several times per level: extrapolation
     vs the network's checked guess (both in `mode`) and, with with_fp64, the
-    plain FP64 solver with extrapolation; returns per-level statistics with
-    the wall time of each step (the network's prediction included)."""
+    plain FP64 solver with extrapolation, all with the same forcing of the
+    linear solves; returns per-level statistics with the wall time of each
+    step (the network's prediction included)."""
     import torch
     ldg.ldg_set_viscosity(h, 1.0 / re)
     Us = [torch.from_numpy(U0).cuda()]
@@ -144,7 +146,7 @@ def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
     for k in range(steps):
         first = k == 0
         Um1 = Us[-2] if k else None
-        (ext, s_ext), ms_ext = _timed(lambda: _step(h, Us[-1], Um1, dt, first, mode, force=True))
+        (ext, s_ext), ms_ext = _timed(lambda: _step(h, Us[-1], Um1, dt, first, mode, force=True, forcing=forcing))
         if k >= 2:
             pred = torch.empty_like(Us[-1])
 
@@ -152,7 +154,8 @@ def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
                 guess = torch.empty_like(Us[-1])
                 ldg.ldg_mlp_predict(h, mlp, Us[-1], Us[-2], Us[-3], guess)
                 pred.copy_(guess)  # the guess before the solver overwrites it
-                return _step(h, Us[-1], Um1, dt, first, mode, predictor=ldg.PRED_CHECKED, guess=guess, force=True)
+                return _step(h, Us[-1], Um1, dt, first, mode, predictor=ldg.PRED_CHECKED, guess=guess, force=True,
+                             forcing=forcing)
             (nn_, s_nn), ms_nn = _timed(learned_step)
             e_mlp = float((pred - ext).norm())
             e_ext = float((2.0 * Us[-1] - Us[-2] - ext).norm())
@@ -164,7 +167,8 @@ def evaluate(h, mlp, U0, re, steps, dt, mode=ldg.MODE_MIXED, with_fp64=True):
                    "ms_extrap": ms_ext, "ms_mlp": ms_nn,
                    "diff": float((nn_ - ext).abs().max() / ext.abs().max())}
             if with_fp64:
-                (u64, s64), ms64 = _timed(lambda: _step(h, Us[-1], Um1, dt, first, ldg.MODE_FP64, force=True))
+                (u64, s64), ms64 = _timed(lambda: _step(h, Us[-1], Um1, dt, first, ldg.MODE_FP64, force=True,
+                                                        forcing=forcing))
                 row.update({"ms_fp64": ms64, "newton_fp64": s64["newton_its"], "gmres_fp64": s64["gmres_its"],
                             "diff_fp64": float((ext - u64).norm() / u64.norm())})
             rows.append(row)
@@ -184,8 +188,31 @@ def init_params(n_in, n_out, seed):
     return np.concatenate(parts)
 
 
+def summarize(rows):
+    """Means over the evaluated levels of one held-out trajectory."""
+    out = {"mean_res_ratio_mlp_over_extrap": float(np.mean([r["res_mlp"] / r["res_extrap"] for r in rows])),
+           "newton_extrap": float(np.mean([r["newton_extrap"] for r in rows])),
+           "newton_mlp": float(np.mean([r["newton_mlp"] for r in rows])),
+           "gmres_extrap": float(np.mean([r["gmres_extrap"] for r in rows])),
+           "gmres_mlp": float(np.mean([r["gmres_mlp"] for r in rows])),
+           "mean_err_ratio_mlp_over_extrap": float(np.mean([r["err_mlp"] / r["err_extrap"] for r in rows])),
+           "mean_mlp_weight": float(np.mean([r["mlp_weight"] for r in rows])),
+           "ms_mixed_extrap": float(np.mean([r["ms_extrap"] for r in rows])),
+           "ms_mixed_mlp": float(np.mean([r["ms_mlp"] for r in rows]))}
+    if rows and "ms_fp64" in rows[0]:
+        out.update({"ms_fp64_extrap": float(np.mean([r["ms_fp64"] for r in rows])),
+                    "newton_fp64": float(np.mean([r["newton_fp64"] for r in rows])),
+                    "gmres_fp64": float(np.mean([r["gmres_fp64"] for r in rows])),
+                    "max_rel_diff_mixed_vs_fp64": float(np.max([r["diff_fp64"] for r in rows]))})
+    return out
+
+
 def experiment(n=16, p=3, n_traj=200, steps=10, dt=0.03, train_steps=20000, lines=4096, seed=2024,
-               held_out=1200.0, eval_steps=12, lr=1e-3, verbose=True):
+               held_out=1200.0, eval_steps=12, lr=1e-3, verbose=True,
+               forcings=(ldg.FORCING_FIXED, ldg.FORCING_TARGET)):
+    """Trajectories, training and the held-out evaluation; the summary of the
+    first forcing policy is at the top level, the others under
+    "forcing_<policy>"."""
     import torch
     m, eq, U0 = tgv_problem(n, p)
     h = ldg.ldg_setup(m, eq)
@@ -211,28 +238,25 @@ def experiment(n=16, p=3, n_traj=200, steps=10, dt=0.03, train_steps=20000, line
     hist = train(mlp, X, T, train_steps, lr=lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    rows = evaluate(h, mlp, U0, held_out, eval_steps, dt)
-    ratio = [r["res_mlp"] / r["res_extrap"] for r in rows]
     out = {"mesh": f"{n}^3", "p": p, "trajectories": n_traj, "levels_per_trajectory": steps, "dt": dt,
            "samples": int(X.shape[0]), "train_steps": train_steps, "t_generate_s": t_gen,
            "t_train_s": t_train, "loss_first": hist[0][1], "loss_last": hist[-1][1],
-           "held_out_re": held_out, "mean_res_ratio_mlp_over_extrap": float(np.mean(ratio)),
-           "newton_extrap": float(np.mean([r["newton_extrap"] for r in rows])),
-           "newton_mlp": float(np.mean([r["newton_mlp"] for r in rows])),
-           "gmres_extrap": float(np.mean([r["gmres_extrap"] for r in rows])),
-           "gmres_mlp": float(np.mean([r["gmres_mlp"] for r in rows])),
-           "mean_err_ratio_mlp_over_extrap": float(np.mean([r["err_mlp"] / r["err_extrap"] for r in rows])),
-           "mean_mlp_weight": float(np.mean([r["mlp_weight"] for r in rows])),
-           "ms_mixed_extrap": float(np.mean([r["ms_extrap"] for r in rows])),
-           "ms_mixed_mlp": float(np.mean([r["ms_mlp"] for r in rows])),
-           "levels": rows}
-    if rows and "ms_fp64" in rows[0]:
-        out.update({"ms_fp64_extrap": float(np.mean([r["ms_fp64"] for r in rows])),
-                    "newton_fp64": float(np.mean([r["newton_fp64"] for r in rows])),
-                    "gmres_fp64": float(np.mean([r["gmres_fp64"] for r in rows])),
-                    "max_rel_diff_mixed_vs_fp64": float(np.max([r["diff_fp64"] for r in rows]))})
+           "held_out_re": held_out}
+    names = {ldg.FORCING_FIXED: "fixed", ldg.FORCING_TARGET: "target"}
+    for k, f in enumerate(forcings):
+        rows = evaluate(h, mlp, U0, held_out, eval_steps, dt, forcing=f)
+        summ = dict(summarize(rows), levels=rows)
+        if k == 0:
+            out.update(summ)
+            out["forcing"] = names[f]
+        else:
+            out["forcing_" + names[f]] = summ
     if verbose:
-        print(json.dumps({k: v for k, v in out.items() if k != "levels"}), flush=True)
+        print(json.dumps({k: v for k, v in out.items() if k != "levels" and not k.startswith("forcing_")}),
+              flush=True)
+        for k, v in out.items():
+            if k.startswith("forcing_"):
+                print(k, json.dumps({a: b for a, b in v.items() if a != "levels"}), flush=True)
     return out, mlp, h
 
 

@@ -275,7 +275,17 @@ def test_preconditioner_factors_and_apply(L, name, prec):
     z = torch.empty_like(rt)
     L.ldg_precond_apply(h, P, rt, z, prec)
     torch.cuda.synchronize()
-    assert np.abs(z.double().cpu().numpy() - zo).max() / np.abs(zo).max() < (1e-4 if prec == 0 else 1e-10)
+    zg = z.double().cpu().numpy()
+    # end to end against the FP64 factors: the triangular solves amplify the
+    # factors' FP32 rounding (1e-5 above), hence 1e-4 here
+    assert np.abs(zg - zo).max() / np.abs(zo).max() < (1e-4 if prec == 0 else 1e-10)
+    # the apply alone: the oracle's triangular solves in FP64 on the GPU's own
+    # factors and the rounded input, so only the apply's own arithmetic differs
+    Fd = np.zeros_like(Fo)
+    for i in range(disc.npe):
+        Fd[:, i, pat[i]] = Fg[:, i]
+    zr = S.ilu_apply(Fd, pat, rt.double().cpu().numpy())
+    assert np.abs(zg - zr).max() / np.abs(zr).max() < (1e-5 if prec == 0 else 1e-12)
 
 
 @pytest.mark.parametrize("mode", [0, 1])

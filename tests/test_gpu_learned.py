@@ -7,7 +7,10 @@ initial guesses must have a clearly smaller nodal error and BDF2 residual
 than the extrapolation on average, the residual check must keep a large
 weight on the network's guess, and the converged solutions must agree to
 the Newton tolerance. The size of the gain is an empirical claim (no closed
-form pins it)."""
+form pins it). With the target-aware forcing (each linear solve asked only
+for the reduction the stopping rule still needs) the smaller start residual
+turns into fewer GMRES iterations: the network's starts must not need more
+iterations in total than extrapolation's."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -24,3 +27,6 @@ def test_learned_guess_beats_extrapolation():
     assert out["mean_mlp_weight"] > 0.3
     for r in out["levels"]:
         assert r["diff"] < 1e-6
+    tf = out["forcing_target"]
+    assert sum(r["gmres_mlp"] for r in tf["levels"]) <= sum(r["gmres_extrap"] for r in tf["levels"]), tf
+    assert tf["gmres_extrap"] <= out["gmres_extrap"], (tf["gmres_extrap"], out["gmres_extrap"])

@@ -101,12 +101,14 @@ def test_coupled_solve_matches_direct_solve(L, name):
 
 
 def test_stabilised_rates_and_zero_c22_on_gpu(L):
-    """Table 2 on the GPU (unstructured mesh refined uniformly, p = 3): the
-    stabilised scheme keeps u's rate near p + 1 and lifts q's rate above the
-    minimal-dissipation rate of Table 2's upper half. With C22 = 0 the same
-    coupled solve reproduces the reduced steady solve's U (once-refined
-    mesh: on the twice-refined one GMRES with element-local preconditioners
-    stagnates for the minimal-dissipation operator, in the oracle too)."""
+    """Table 2's lower half on the GPU (p = 3, the paper's manufactured
+    solution with its Dirichlet data on the nested mapped squares n = 4 .. 32,
+    three refinement pairs): the stabilised scheme keeps u's rate near p + 1
+    and lifts q's rate above the minimal-dissipation rate of the table's upper
+    half. With C22 = 0 the same coupled solve reproduces the reduced steady
+    solve's U (once-refined unstructured mesh: on the twice-refined one GMRES
+    with element-local preconditioners stagnates for the minimal-dissipation
+    operator, in the oracle too)."""
     import os
 
     import torch
@@ -114,30 +116,36 @@ def test_stabilised_rates_and_zero_c22_on_gpu(L):
     gold = np.loadtxt(os.path.join(here, "golden", "poisson_rates_stabilized.txt"), comments="#")
     gold0 = np.loadtxt(os.path.join(here, "golden", "poisson_rates.txt"), comments="#")
     errs = []
-    for refine in (0, 1, 2):
-        m = I.unstructured_quad_mesh(2, 3, perturb=0.15, refine=refine)
+    for n in (4, 8, 16, 32):
+        m = I.poisson_mapped_square_mesh(n, 3)
         E, npe = m["nodes"].shape[:2]
-        f = I.poisson_source(m)
-        for c in ((C, 0.0) if refine == 1 else (C,)):
-            eq = {"kind": "poisson", "C11": c, "C22": c, "C11b": 1.0, "bc": {0: "dirichlet"}, "source": f,
-                  "gD": np.zeros_like(f)}
-            h = L.ldg_setup(m, eq)
-            U = torch.zeros((E, 1, npe), dtype=torch.float64, device="cuda")
-            Q = torch.zeros((E, 1, 2, npe), dtype=torch.float64, device="cuda")
-            st = L.ldg_coupled_solve(h, U, Q, rtol=1e-11, restart=64, max_cycles=100)
-            assert st["res_final"] <= 1e-11 * st["res0"]
-            if c == C:
-                errs.append((np.abs(U.cpu().numpy() - I.poisson_exact(m)).max(),
-                             np.abs(Q.cpu().numpy() - I.poisson_exact_grad(m)).max()))
-            else:
-                Ur = torch.zeros_like(U)
-                L.ldg_steady_solve(h, Ur, 1.0, 1.0, 0, L.solver_opts(mode=0, rtol=1e-12, max_newton=30, restart=64))
-                assert float((Ur - U).abs().max()) <= 1e-8 * float(U.abs().max())
-    ru = math.log2(errs[1][0] / errs[2][0])
-    rq = math.log2(errs[1][1] / errs[2][1])
-    assert abs(ru - gold[2][3]) < 0.6, (errs, ru)
-    assert abs(rq - gold[2][6]) < 0.6, (errs, rq)
-    assert rq > gold0[2][6] + 0.2, (errs, rq)
+        u, gu, f = I.poisson_paper_solution(m)
+        eq = {"kind": "poisson", "C11": C, "C22": C, "C11b": 1.0, "bc": {0: "dirichlet"}, "source": f, "gD": u}
+        h = L.ldg_setup(m, eq)
+        U = torch.zeros((E, 1, npe), dtype=torch.float64, device="cuda")
+        Q = torch.zeros((E, 1, 2, npe), dtype=torch.float64, device="cuda")
+        st = L.ldg_coupled_solve(h, U, Q, rtol=1e-11, restart=64, max_cycles=200)
+        assert st["res_final"] <= 1e-11 * st["res0"]
+        errs.append((np.abs(U.cpu().numpy() - u).max(), np.abs(Q.cpu().numpy() - gu).max()))
+    ru = np.mean([math.log2(errs[k][0] / errs[k + 1][0]) for k in range(3)])
+    rq = np.mean([math.log2(errs[k][1] / errs[k + 1][1]) for k in range(3)])
+    assert abs(ru - np.mean(gold[2][1:4])) < 0.3, (errs, ru)
+    assert abs(rq - np.mean(gold[2][4:7])) < 0.3, (errs, rq)
+    assert rq > np.mean(gold0[2][4:7]) + 0.2, (errs, rq)
+    # C22 = 0: the coupled solve is the reduced steady solve
+    m = I.unstructured_quad_mesh(2, 3, perturb=0.15, refine=1)
+    E, npe = m["nodes"].shape[:2]
+    f = I.poisson_source(m)
+    eq = {"kind": "poisson", "C11": 0.0, "C22": 0.0, "C11b": 1.0, "bc": {0: "dirichlet"}, "source": f,
+          "gD": np.zeros_like(f)}
+    h = L.ldg_setup(m, eq)
+    U = torch.zeros((E, 1, npe), dtype=torch.float64, device="cuda")
+    Q = torch.zeros((E, 1, 2, npe), dtype=torch.float64, device="cuda")
+    st = L.ldg_coupled_solve(h, U, Q, rtol=1e-11, restart=64, max_cycles=100)
+    assert st["res_final"] <= 1e-11 * st["res0"]
+    Ur = torch.zeros_like(U)
+    L.ldg_steady_solve(h, Ur, 1.0, 1.0, 0, L.solver_opts(mode=0, rtol=1e-12, max_newton=30, restart=64))
+    assert float((Ur - U).abs().max()) <= 1e-8 * float(U.abs().max())
 
 
 def test_stabilised_handle_refuses_the_reduced_calls(L):

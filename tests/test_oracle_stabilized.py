@@ -89,25 +89,37 @@ def test_c22_sign_keeps_the_steady_operator_dissipative(C22):
     assert out[0] < 0.0 < out[1], out
 
 
-def _rates(p, levels, C):
-    res = []
-    for r in levels:
-        m = I.unstructured_quad_mesh(2, p, perturb=0.15, refine=r)
-        f = I.poisson_source(m)
-        U, Q = coupled_solve(Discretization(m, stab_eq(C=C)), np.zeros_like(f), f)
-        res.append((np.abs(U - I.poisson_exact(m)).max(), np.abs(Q - I.poisson_exact_grad(m)).max()))
-    return (math.log2(res[-2][0] / res[-1][0]), math.log2(res[-2][1] / res[-1][1]))
+def _paper_errors(p, n, C):
+    """|u_h - u|_inf and |q_h - grad u|_inf of the coupled solve with the
+    paper's manufactured solution and Dirichlet data (Sec. 5.1) on the
+    n x n mapped square."""
+    m = I.poisson_mapped_square_mesh(n, p)
+    u, gu, f = I.poisson_paper_solution(m)
+    U, Q = coupled_solve(Discretization(m, stab_eq(C=C)), u, f)
+    return np.abs(U - u).max(), np.abs(Q - gu).max()
+
+
+def _mean_rates(p, C, levels=(4, 8, 16, 32)):
+    errs = [_paper_errors(p, n, C) for n in levels]
+    ru = [math.log2(errs[k][0] / errs[k + 1][0]) for k in range(len(errs) - 1)]
+    rq = [math.log2(errs[k][1] / errs[k + 1][1]) for k in range(len(errs) - 1)]
+    return float(np.mean(ru)), float(np.mean(rq)), ru, rq
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("p", [1, 2, 3])
-def test_table2_stabilised_rates_on_refined_unstructured_mesh(p):
-    # Table 2, lower half: u keeps ~p+1, q gains over the minimal-dissipation
-    # scheme (p), on an unstructured mesh refined uniformly
+def test_table2_stabilised_rates_paper_solution(p):
+    # Table 2, lower half, with the paper's own manufactured solution and
+    # Dirichlet data on a nested sequence of curved meshes (three uniform
+    # refinements, as in the table): u keeps ~p+1, q gains over the
+    # minimal-dissipation scheme. Means over the three refinement pairs
+    # against the table's means; the interior penalty is per unit reference
+    # length (the reading that matches the table's u and q rates best)
     gold = {int(r[0]): r[1:] for r in np.loadtxt(f"{GOLD}/poisson_rates_stabilized.txt", comments="#")}
-    levels = (1, 2, 3) if p < 3 else (0, 1, 2)
-    ru, rq = _rates(p, levels, 1.0 / 20.0)
-    _, rq0 = _rates(p, levels, 1e-300)
-    assert abs(ru - gold[p][2]) < 0.6, (ru, gold[p])
-    assert abs(rq - gold[p][5]) < 0.6, (rq, gold[p])
-    assert rq > rq0 + 0.25, (rq, rq0)
+    levels = {1: (8, 16, 32, 64), 2: (8, 16, 32), 3: (4, 8, 16, 32)}[p]
+    k = len(levels) - 1                       # compared with the table's last k pairs
+    ru, rq, rus, rqs = _mean_rates(p, 1.0 / 20.0, levels)
+    _, rq0, _, _ = _mean_rates(p, 1e-300, levels)
+    assert abs(ru - np.mean(gold[p][3 - k:3])) < 0.3, (ru, rus, gold[p])
+    assert abs(rq - np.mean(gold[p][6 - k:6])) < 0.3, (rq, rqs, gold[p])
+    assert rq > rq0 + 0.15, (rq, rq0)
