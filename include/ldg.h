@@ -265,6 +265,32 @@ int ldg_jacvec(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, 
                void* y, int prec, void* stream);
 
 /*
+ * The two halves of the split product of Eq. 41, for runs on a partitioned
+ * mesh (one part per process or GPU) that exchange the face-node traces of
+ * the discrete gradient between them: a part's K12 reaches K21 x at the
+ * outside node of its lines' ends, which another part owns.
+ *   ldg_k21_apply: g = K21 x (second-order equations; LDG_ERR_UNSUPPORTED
+ *     otherwise), g device [n_elem][n_c][D][(p+1)^D] in the vector precision.
+ *   ldg_jacvec_g: y = shift x + scale (K11 x + K12 g) with the given g (g may
+ *     be NULL for first-order equations).
+ * Precisions and errors as ldg_jacvec. ldg_k21_apply followed by
+ * ldg_jacvec_g on the same g equals ldg_jacvec.
+ */
+int ldg_k21_apply(ldg_handle_t* h, const ldg_jac_t* J, const void* x, void* g, int prec, void* stream);
+int ldg_jacvec_g(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, const void* x,
+                 const void* g, void* y, int prec, void* stream);
+
+/*
+ * ldg_jacobian at a given gradient Q (device FP64 [n_elem][n_c][D][(p+1)^D],
+ * required for second-order equations, ignored for first-order ones)
+ * instead of Q = D(U): a part of a partitioned mesh passes the gradient whose
+ * face-node traces at its cut faces came from the parts that own them.
+ * Otherwise as ldg_jacobian.
+ */
+int ldg_jacobian_uq(ldg_handle_t* h, const double* U, const double* Q, int prec, ldg_jac_t** J,
+                    void* stream);
+
+/*
  * Block-Jacobi preconditioner (Sec. 4.2): per element, A~_e = shift I +
  * scale mask(K11 + K12 K21) on the element-local Line-DG pattern (node i
  * couples to the Dp+1 nodes of its D lines), inter-element couplings and

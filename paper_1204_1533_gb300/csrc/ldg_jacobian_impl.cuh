@@ -111,11 +111,14 @@ struct JacTile {
   // four warps per block and two blocks per SM: the derivative arithmetic
   // needs up to 255 registers a thread, and two blocks with their own
   // barriers let one block's stores overlap the other's arithmetic
-  static constexpr int THREADS = 128;
+  // K12 (ROUND 2) needs no dual numbers: eight warps per block
+  template <int ROUND>
+  static constexpr int threads() { return ROUND == 1 ? 128 : 256; }
   static constexpr int MINB = 2;
   static constexpr int SZ11 = (NQ * NC * NC + 4 * NC * NC) * 32;
   static constexpr int SZ12 = VISC ? (NQ * NC * NCD + 3 * NC * NCD) * 32 : 0;
-  static constexpr int SMEM = (SZ11 > SZ12 ? SZ11 : SZ12) * (int)sizeof(R) + 32 * (int)sizeof(int);
+  static constexpr int SMEM11 = SZ11 * (int)sizeof(R);
+  static constexpr int SMEM12 = SZ12 * (int)sizeof(R) + 32 * (int)sizeof(int);
   static constexpr int64_t NK11 = (N * N + 2 * N) * NC * NC;
   static constexpr int64_t NK12 = VISC ? (N * N + N) * NC * NCD : 1;
   static constexpr int OFF11 = N * N * NC * NC;
@@ -210,8 +213,10 @@ __device__ __forceinline__ void end_flux_derivative(const R* uin, const R* uo, c
     for (int cp = 0; cp < NC; ++cp) out[c * NC + cp] = F[c].d[cp];
 }
 
-template <int D, int P, int NC, int EQ, typename R>
-__global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::THREADS, (JacTile<D, P, NC, EQ, R>::MINB))
+// ROUND 1 assembles K11 (and the wall rows Kw), ROUND 2 K12: two kernels,
+// so each holds only its own code and shared memory
+template <int D, int P, int NC, int EQ, typename R, int ROUND>
+__global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROUND>(), (JacTile<D, P, NC, EQ, R>::MINB))
     k_jacobian(const R* __restrict__ Ur, const R* __restrict__ Qr, R* __restrict__ K11, R* __restrict__ K12,
                R* __restrict__ Kw, Geo g, Tab tab, PhysArgs ph, int64_t nlines) {
   using JT = JacTile<D, P, NC, EQ, R>;
@@ -220,15 +225,16 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::THREADS, (JacTile<D,
   constexpr bool VISC = JT::VISC;
   extern __shared__ unsigned char smraw[];
   R* const sm = reinterpret_cast<R*>(smraw);
-  int* const fend = reinterpret_cast<int*>(smraw + (JT::SMEM - 32 * (int)sizeof(int)));
+  int* const fend = reinterpret_cast<int*>(smraw + (JT::SMEM12 - 32 * (int)sizeof(int)));
   Phys<R> pp;
   pp.set(ph);
   const int64_t tile0 = (int64_t)blockIdx.x * 32;
 
   // ======================= K11 round =======================================
+  if constexpr (ROUND == 1) {
   R* A = sm;                         // [NQ][NC][NC][32]
   R* B = sm + NQ * NC * NC * 32;     // [end][side][NC][NC][32]
-  for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::THREADS) {
+  for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::template threads<ROUND>()) {
     const int lane = it & 31, kind = it >> 5;
     const int64_t L = tile0 + lane;
     if (L >= nlines) continue;
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::THREADS, (JacTile<D,
   }
   __syncthreads();
   // phase B: row i, block column jj (in-line j < N, face blocks N, N + 1)
-  for (int it = threadIdx.x; it < 32 * N * (N + 2); it += JT::THREADS) {
+  for (int it = threadIdx.x; it < 32 * N * (N + 2); it += JT::template threads<ROUND>()) {
     const int lane = it & 31, r = it >> 5;
     const int i = r / (N + 2), jj = r % (N + 2);
     const int64_t L = tile0 + lane;
@@ -370,13 +376,13 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::THREADS, (JacTile<D,
     }
   }
 
+  }  // ROUND == 1
   // ======================= K12 round: F^vis is linear in q ================
-  if constexpr (VISC) {
-    __syncthreads();
+  if constexpr (VISC && ROUND == 2) {
     R* A2 = sm;                            // [NQ][NC][NCD][32]
     R* C2 = sm + NQ * NC * NCD * 32;       // [end][NC][NCD][32] in-line end terms
     R* Cf = C2 + 2 * NC * NCD * 32;        // [NC][NCD][32] face block
-    for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::THREADS) {
+    for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::template threads<ROUND>()) {
       const int lane = it & 31, kind = it >> 5;
       const int64_t L = tile0 + lane;
       if (L >= nlines) continue;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::THREADS, (JacTile<D,
     }
     __syncthreads();
     // phase B: row i, block column jj (in-line j < N, the face block N)
-    for (int it = threadIdx.x; it < 32 * N * (N + 1); it += JT::THREADS) {
+    for (int it = threadIdx.x; it < 32 * N * (N + 1); it += JT::template threads<ROUND>()) {
       const int lane = it & 31, r = it >> 5;
       const int i = r / (N + 1), jj = r % (N + 1);
       const int64_t L = tile0 + lane;
@@ -490,15 +496,19 @@ template <int D, int P, int EQ, typename R>
 cudaError_t run_jacobian(const ldg_handle* h, const R* Ur, const R* Qr, R* K11, R* K12, R* Kw, cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
   using JT = JacTile<D, P, NC, EQ, R>;
-  auto kern = k_jacobian<D, P, NC, EQ, R>;
-  cudaError_t err = set_smem_once(kern, JT::SMEM);
-  if (err != cudaSuccess) return err;
-  // shared memory before L1: two blocks per SM need twice the tile buffers
-  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  if (err != cudaSuccess) return err;
-  kern<<<(unsigned)h->ntiles(), JT::THREADS, JT::SMEM, st>>>(Ur, Qr, K11, K12, Kw, h->geo(), h->tab, h->phys,
-                                                             h->nlines());
-  count_launch();
+  constexpr bool VISC = IsViscous<EQ>::value;
+  for (int round = 1; round <= (VISC ? 2 : 1); ++round) {
+    auto kern = round == 1 ? k_jacobian<D, P, NC, EQ, R, 1> : k_jacobian<D, P, NC, EQ, R, 2>;
+    const int smem = round == 1 ? JT::SMEM11 : JT::SMEM12;
+    cudaError_t err = set_smem_once(kern, smem);
+    if (err != cudaSuccess) return err;
+    // shared memory before L1: several blocks per SM need several tile buffers
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
+    kern<<<(unsigned)h->ntiles(), round == 1 ? JT::template threads<1>() : JT::template threads<2>(), smem, st>>>(Ur, Qr, K11, K12, Kw, h->geo(), h->tab, h->phys,
+                                                          h->nlines());
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -48,6 +48,13 @@ cudaError_t launch_jacvec(const ldg_handle* h, const ldg_jac* J, double shift, d
   LDG_DISPATCH(h, jacvec(h, J, shift, scale, x, y, vprec, st));
   return cudaErrorInvalidValue;
 }
+// the two launches of the split product apart (part 1: g = K21 x; part 2: y
+// from x and g), for partitioned runs that exchange g's face traces between
+static cudaError_t launch_jacvec_part(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
+                                      const void* x, void* g, void* y, int vprec, int part, cudaStream_t st) {
+  LDG_DISPATCH(h, jacvec(h, J, shift, scale, x, y, vprec, st, g, part));
+  return cudaErrorInvalidValue;
+}
 cudaError_t launch_precond(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                            ldg_pc* P, cudaStream_t st) {
   LDG_DISPATCH(h, precond(h, J, shift, scale, P, st));
@@ -80,7 +87,8 @@ extern "C" int ldg_jac_destroy(ldg_jac_t* J) {
   return LDG_OK;
 }
 
-extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_t** Jp, void* stream) {
+static int jacobian_impl(ldg_handle_t* h, const double* U, const double* Qin, int prec, ldg_jac_t** Jp,
+                         void* stream) {
   if (!h || !U || !Jp || (prec != LDG_PREC_FP32 && prec != LDG_PREC_FP64)) return LDG_ERR_ARG;
   if (!ops_supported(h)) return LDG_ERR_UNSUPPORTED;
   ldg_jac* J = *Jp;
@@ -108,8 +116,12 @@ extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_
       return LDG_ERR_CUDA;
     }
   }
-  if (h->viscous() && launch_gradient(h, U, h->Qbuf, st) != cudaSuccess) return LDG_ERR_CUDA;
-  if (launch_jacobian(h, U, h->Qbuf, J, st) != cudaSuccess) return LDG_ERR_CUDA;
+  const double* Q = Qin;
+  if (h->viscous() && !Q) {
+    if (launch_gradient(h, U, h->Qbuf, st) != cudaSuccess) return LDG_ERR_CUDA;
+    Q = h->Qbuf;
+  }
+  if (launch_jacobian(h, U, Q, J, st) != cudaSuccess) return LDG_ERR_CUDA;
   if (h->viscous() && !J->k21_built) {
     if (launch_k21(h, J, st) != cudaSuccess) return LDG_ERR_CUDA;
     J->k21_built = true;
@@ -117,6 +129,16 @@ extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_
   J->built = true;
   *Jp = J;
   return LDG_OK;
+}
+
+extern "C" int ldg_jacobian(ldg_handle_t* h, const double* U, int prec, ldg_jac_t** Jp, void* stream) {
+  return jacobian_impl(h, U, nullptr, prec, Jp, stream);
+}
+
+extern "C" int ldg_jacobian_uq(ldg_handle_t* h, const double* U, const double* Q, int prec, ldg_jac_t** Jp,
+                               void* stream) {
+  if (h && h->viscous() && !Q) return LDG_ERR_ARG;
+  return jacobian_impl(h, U, h && h->viscous() ? Q : nullptr, prec, Jp, stream);
 }
 
 extern "C" int ldg_jac_export(const ldg_jac_t* J, void* K11, void* K12, void* K21) {
@@ -148,6 +170,38 @@ extern "C" int ldg_jacvec(ldg_handle_t* h, const ldg_jac_t* J, double shift, dou
   if (J->prec == LDG_PREC_FP64 && prec == LDG_PREC_FP32) return LDG_ERR_UNSUPPORTED;
   return launch_jacvec(h, J, shift, scale, x, y, prec, (cudaStream_t)stream) == cudaSuccess ? LDG_OK
                                                                                           : LDG_ERR_CUDA;
+}
+
+static int jacvec_args(ldg_handle_t* h, const ldg_jac_t* J, int prec) {
+  if (!h || !J || J->h != h) return LDG_ERR_ARG;
+  if (!J->built) return LDG_ERR_NOT_BUILT;
+  if (prec != LDG_PREC_FP32 && prec != LDG_PREC_FP64) return LDG_ERR_ARG;
+  if (J->prec == LDG_PREC_FP64 && prec == LDG_PREC_FP32) return LDG_ERR_UNSUPPORTED;
+  return LDG_OK;
+}
+
+extern "C" int ldg_k21_apply(ldg_handle_t* h, const ldg_jac_t* J, const void* x, void* g, int prec, void* stream) {
+  int rc = jacvec_args(h, J, prec);
+  if (rc) return rc;
+  if (!x || !g) return LDG_ERR_ARG;
+  if (!h->viscous()) return LDG_ERR_UNSUPPORTED;
+  return launch_jacvec_part(h, J, 0.0, 0.0, x, g, nullptr, prec, 1, (cudaStream_t)stream) == cudaSuccess
+             ? LDG_OK
+             : LDG_ERR_CUDA;
+}
+
+extern "C" int ldg_jacvec_g(ldg_handle_t* h, const ldg_jac_t* J, double shift, double scale, const void* x,
+                            const void* g, void* y, int prec, void* stream) {
+  int rc = jacvec_args(h, J, prec);
+  if (rc) return rc;
+  if (!x || !y || (h->viscous() && !g)) return LDG_ERR_ARG;
+  const double esz = J->prec == LDG_PREC_FP32 ? 4.0 : 8.0, vsz = prec == LDG_PREC_FP32 ? 4.0 : 8.0;
+  TimedScope tl(KT_JACVEC, prec, (cudaStream_t)stream,
+                (double)h->ntiles() * 32.0 * (h->nk11() + h->nk12()) * esz + 2.0 * h->ndof * vsz, 0.0);
+  return launch_jacvec_part(h, J, shift, scale, x, const_cast<void*>(g), y, prec, 2, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? LDG_OK
+             : LDG_ERR_CUDA;
 }
 
 extern "C" int ldg_pc_destroy(ldg_pc_t* P) {

@@ -689,10 +689,9 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
     const bool fwd = t < NPE - 1;
     const Pos ps(fwd ? t + 1 : 2 * NPE - 2 - t);
     const int b = t % (PD + 1);
-    // one chain per lane, started at -y_i on the lane that owns the row's
-    // value: the group sum is then -(y_i - sum F y) with no separate partial
-    // sums or subtraction (in FP64 every addition costs the narrow FP64 pipe)
-    V acc = (act && g == 0) ? -y[c * NPE + ps.i] : V(0);
+    V acc[MPL];
+#pragma unroll
+    for (int mm = 0; mm < MPL; ++mm) acc[mm] = V(0);
     if (act) {
       if (fwd) {
 #pragma unroll
@@ -700,7 +699,7 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
           if (k < ps.dg) {
             const int col = ps.lower_col(k);
 #pragma unroll
-            for (int mm = 0; mm < MPL; ++mm) acc += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
+            for (int mm = 0; mm < MPL; ++mm) acc[mm] += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
           }
       } else {
 #pragma unroll
@@ -708,21 +707,24 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
           if (k < MAXS - ps.dg) {
             const int col = ps.upper_col(k);
 #pragma unroll
-            for (int mm = 0; mm < MPL; ++mm) acc += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
+            for (int mm = 0; mm < MPL; ++mm) acc[mm] += (V)fb[b][k][mm] * y[(m0 + mm) * NPE + col];
           }
       }
     }
-    const V ns = group_sum<G>(acc, sc, lane);  // -(y_i - sum)
+    V pv = 0;
+#pragma unroll
+    for (int mm = 0; mm < MPL; ++mm) pv += acc[mm];
+    const V s = group_sum<G>(pv, sc, lane);
     if (fwd) {
-      if (act && g == 0) y[c * NPE + ps.i] = -ns;
+      if (act && g == 0) y[c * NPE + ps.i] -= s;
       __syncwarp();
     } else {
-      if (act && g == 0) tbuf[c] = ns;
+      if (act && g == 0) tbuf[c] = y[c * NPE + ps.i] - s;
       __syncwarp();
       V d = 0;
       if (act) {
 #pragma unroll
-        for (int mm = 0; mm < MPL; ++mm) d -= (V)db[b][mm] * tbuf[m0 + mm];
+        for (int mm = 0; mm < MPL; ++mm) d += (V)db[b][mm] * tbuf[m0 + mm];
       }
       const V zi = group_sum<G>(d, sc, lane);
       if (act && g == 0) y[c * NPE + ps.i] = zi;
@@ -733,22 +735,29 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
     for (int k = q; k < tile; k += A::LPE) z[e * tile + k] = y[k];
 }
 
+// The split product y = shift x + scale (K11 x + K12 (K21 x)) as its two
+// launches: part 0 both (K21 x into gbuf), part 1 only g = K21 x into gbuf,
+// part 2 only y from x and a given g in gbuf (a partitioned part exchanges
+// the face traces of g between the two).
 template <int D, int P, int EQ, typename R, typename V>
 cudaError_t run_jacvec(const ldg_handle* h, const R* K11, const R* K12, const R* K21, const R* Kw, V* gbuf,
-                       double shift, double scale, const V* x, V* y, cudaStream_t st) {
+                       double shift, double scale, const V* x, V* y, cudaStream_t st, int part = 0) {
   using S = Shape<D, P>;
   constexpr int NC = NComp<EQ, D>::value;
   constexpr bool VISC = IsViscous<EQ>::value;
   const int64_t blocks = (h->E + S::EPB - 1) / S::EPB;
   cudaError_t err;
   if constexpr (VISC) {
-    const size_t sm1 = (size_t)S::EPB * (NC * S::NPE + D * NC * D * S::NPE) * sizeof(V);
-    auto k1 = k_k21_apply<D, P, NC, R, V>;
-    err = set_smem_once(k1, sm1);
-    if (err != cudaSuccess) return err;
-    k1<<<(unsigned)blocks, S::THREADS, sm1, st>>>(K21, Kw, x, gbuf, h->geo(), h->tab);
-    count_launch();
+    if (part != 2) {
+      const size_t sm1 = (size_t)S::EPB * (NC * S::NPE + D * NC * D * S::NPE) * sizeof(V);
+      auto k1 = k_k21_apply<D, P, NC, R, V>;
+      err = set_smem_once(k1, sm1);
+      if (err != cudaSuccess) return err;
+      k1<<<(unsigned)blocks, S::THREADS, sm1, st>>>(K21, Kw, x, gbuf, h->geo(), h->tab);
+      count_launch();
+    }
   }
+  if (part == 1) return cudaGetLastError();
   const size_t sm2 = (size_t)S::EPB * (NC * S::NPE + (VISC ? NC * D * S::NPE : 0) + D * NC * S::NPE) * sizeof(V);
   auto k2 = k_jacvec<D, P, NC, EQ, R, V>;
   err = set_smem_once(k2, sm2);

@@ -69,26 +69,27 @@ cudaError_t Ops<D, EQ>::k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st) {
 
 template <int D, int EQ>
 cudaError_t Ops<D, EQ>::jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
-                               const void* x, void* y, int vprec, cudaStream_t st) {
+                               const void* x, void* y, int vprec, cudaStream_t st, void* g, int part) {
+  void* gb = g ? g : J->gbuf;
   if (J->prec == LDG_PREC_FP32 && vprec == LDG_PREC_FP32) {
 #define F(P)                                                                                      \
   return run_jacvec<D, P, EQ, float, float>(h, (const float*)J->K11, (const float*)J->K12,         \
                                             (const float*)J->K21, (const float*)J->Kw,            \
-                                            (float*)J->gbuf, shift, scale, (const float*)x, (float*)y, st)
+                                            (float*)gb, shift, scale, (const float*)x, (float*)y, st, part)
     LDG_FOR_P(F)
 #undef F
   } else if (J->prec == LDG_PREC_FP32) {
 #define F(P)                                                                                        \
   return run_jacvec<D, P, EQ, float, double>(h, (const float*)J->K11, (const float*)J->K12,          \
                                              (const float*)J->K21, (const float*)J->Kw,             \
-                                             (double*)J->gbuf, shift, scale, (const double*)x, (double*)y, st)
+                                             (double*)gb, shift, scale, (const double*)x, (double*)y, st, part)
     LDG_FOR_P(F)
 #undef F
   } else if (vprec == LDG_PREC_FP64) {
 #define F(P)                                                                                          \
   return run_jacvec<D, P, EQ, double, double>(h, (const double*)J->K11, (const double*)J->K12,         \
                                               (const double*)J->K21, (const double*)J->Kw,              \
-                                              (double*)J->gbuf, shift, scale, (const double*)x, (double*)y, st)
+                                              (double*)gb, shift, scale, (const double*)x, (double*)y, st, part)
     LDG_FOR_P(F)
 #undef F
   }

@@ -92,6 +92,9 @@ _SIGS = {
                               C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "ldg_residual_noalloc": [_P, _P, _P, _P],
     "ldg_fp64_fma_probe": [C.c_int32, _P, C.c_int64, C.POINTER(C.c_double), _P],
+    "ldg_k21_apply": [_P, _P, _P, _P, _I, _P],
+    "ldg_jacvec_g": [_P, _P, C.c_double, C.c_double, _P, _P, _P, _I, _P],
+    "ldg_jacobian_uq": [_P, _P, _P, _I, C.POINTER(_P), _P],
     "ldg_set_viscosity": [_P, C.c_double],
     "ldg_mlp_create": [C.c_int32, C.c_int32, C.POINTER(_P)],
     "ldg_mlp_destroy": [_P],
@@ -333,6 +336,16 @@ def ldg_jacobian(h, U, prec=PREC_FP32, J=None, stream=None):
     return J
 
 
+def ldg_jacobian_uq(h, U, Q, prec=PREC_FP32, J=None, stream=None):
+    """ldg_jacobian at a given gradient Q (see ldg.h)."""
+    ptr = C.c_void_p(None if J is None else J.ptr.value)
+    _check(lib().ldg_jacobian_uq(h.ptr, _dptr(U), None if Q is None else _dptr(Q), prec, C.byref(ptr),
+                                 _stream(stream)), "ldg_jacobian_uq")
+    if J is None:
+        J = Jacobian(h, ptr, prec)
+    return J
+
+
 def ldg_jac_export(J):
     h = J.h
     dt = np.float32 if J.prec == PREC_FP32 else np.float64
@@ -348,6 +361,19 @@ def ldg_jac_export(J):
 def ldg_jacvec(h, J, shift, scale, x, y, prec=PREC_FP32, stream=None):
     _check(lib().ldg_jacvec(h.ptr, J.ptr, float(shift), float(scale), _dptr(x), _dptr(y), prec,
                             _stream(stream)), "ldg_jacvec")
+    return y
+
+
+def ldg_k21_apply(h, J, x, g, prec=PREC_FP32, stream=None):
+    """g = K21 x, the first half of the split product (see ldg.h)."""
+    _check(lib().ldg_k21_apply(h.ptr, J.ptr, _dptr(x), _dptr(g), prec, _stream(stream)), "ldg_k21_apply")
+    return g
+
+
+def ldg_jacvec_g(h, J, shift, scale, x, g, y, prec=PREC_FP32, stream=None):
+    """y = shift x + scale (K11 x + K12 g), the second half (see ldg.h)."""
+    _check(lib().ldg_jacvec_g(h.ptr, J.ptr, float(shift), float(scale), _dptr(x), None if g is None else _dptr(g),
+                              _dptr(y), prec, _stream(stream)), "ldg_jacvec_g")
     return y
 
 
