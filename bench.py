@@ -721,9 +721,39 @@ def learned_section(args):
     extrapolation and mixed + learned guess (residual-checked), all to the
     same 1e-8 relative residual, with the fixed and the target-aware forcing
     of the linear solves."""
+    import torch
+
     from paper_1204_1533_gb300 import learned
-    out, _, h = learned.experiment(n=args.learn_n, n_traj=args.learn_traj, steps=10, dt=args.learn_dt,
-                                   train_steps=args.learn_train, lines=4096, eval_steps=12, verbose=False)
+    from paper_1204_1533_gb300 import ldg
+    out, mlp, h = learned.experiment(n=args.learn_n, n_traj=args.learn_traj, steps=10, dt=args.learn_dt,
+                                     train_steps=args.learn_train, lines=4096, eval_steps=12, verbose=False)
+    # the trained network's inference (tcgen05 tensor cores, TMEM accumulators)
+    # over the direction-1 lines of the 32^3, p = 3 Taylor-Green mesh
+    lines = 32 ** 3 * 16
+    X = torch.randn((lines, ldg.MLP_INP), device="cuda").to(torch.bfloat16)
+    Y = torch.empty((lines, mlp.n_out), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ldg.ldg_mlp_forward(mlp, X, Y)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(st)
+    for _ in range(reps):
+        ldg.ldg_mlp_forward(mlp, X, Y)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * lines * (mlp.n_in * 128 + 2 * 128 * 128 + 128 * mlp.n_out)
+    byts = lines * (ldg.MLP_INP * 2 + mlp.n_out * 4)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        bf16_peak = 1900.0
+    hbm, _ = _peaks()
+    inference = {"kernel": "k_mlp_fwd_tc (tcgen05.mma kind::f16, TMEM accumulators)", "lines": lines, "ms": ms,
+                 "tflops": flops / (ms * 1e-3) / 1e12, "frac_bf16_peak": flops / (ms * 1e-3) / 1e12 / bf16_peak,
+                 "gbs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm}
     keep = ("mesh", "p", "trajectories", "levels_per_trajectory", "dt", "samples", "train_steps", "t_generate_s",
             "t_train_s", "loss_first", "loss_last", "held_out_re", "mean_res_ratio_mlp_over_extrap",
             "mean_err_ratio_mlp_over_extrap", "mean_mlp_weight", "newton_extrap", "newton_mlp", "newton_fp64",
@@ -743,6 +773,7 @@ def learned_section(args):
             t["speedup_mixed_learned_vs_fp64"] = t["ms_fp64_extrap"] / t["ms_mixed_mlp"]
             t["speedup_mixed_learned_vs_mixed_extrap"] = t["ms_mixed_extrap"] / t["ms_mixed_mlp"]
         res["forcing_target"] = t
+    res["inference_32cubed"] = inference
     return res
 
 

@@ -1,5 +1,8 @@
 // Line-local MLP Newton predictor: features, fused forward / backward on
 // BF16 tensor cores with FP32 accumulation, Adam, prediction scatter.
+// Inference (ldg_mlp_forward, ldg_mlp_predict) runs on the tcgen05 tensor
+// cores with tensor-memory accumulators (k_mlp_fwd_tc below); training runs
+// the fused forward + backward tile kernel described next.
 //
 // Network n_in -> 128 -> 128 -> 128 -> n_out with GELU (tanh form of
 // Hendrycks and Gimpel), n_in <= 96, n_out <= 32. One block of 4 warps
@@ -420,6 +423,270 @@ __global__ void k_pack(const float* __restrict__ theta, int nin, int nout, bf16*
 }
 
 // ---------------------------------------------------------------------------
+// Forward pass on the fifth-generation tensor cores (tcgen05): one CTA of 4
+// warps per tile of 128 lines (the MMA's M), persistent over the tiles. The
+// four weight matrices are packed once (k_pack) in the canonical K-major
+// layout without swizzling -- core matrices of 8 rows x 16 bytes, element
+// (r, k) of an R x K operand at byte ((r/8)(K/8) + k/8) 128 + (r%8) 16 +
+// (k%8) 2 -- and copied to shared memory by bulk asynchronous copies (TMA)
+// completing on an mbarrier. Each layer is a chain of
+// tcgen05.mma.cta_group::1.kind::f16 (BF16 operands from shared memory, FP32
+// accumulator of 128 lanes x N columns in tensor memory, K = 16 per
+// instruction) issued by one thread and committed to an mbarrier; every
+// thread then reads its row of the accumulator (tcgen05.ld, warp w owns
+// lanes 32w .. 32w + 31), adds the bias, applies GELU and writes the BF16
+// activation in the same canonical layout as the next layer's A operand.
+// Every wait is bounded: on a timeout the tile's outputs are NaN and the
+// error flag is set; tensor memory is released in every case.
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int TM = 128;          // lines per tile (the MMA's M)
+constexpr int TTHREADS = 128;    // one thread per row of the tile
+constexpr int TMEM_COLS = 128;   // the accumulator: 128 lanes x 128 FP32 columns
+constexpr long WAIT_LIMIT = 1L << 22;
+
+__host__ __device__ constexpr int coff(int r, int k, int K) {
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+struct __align__(1024) Smem {
+  unsigned char W1[HID * INP * 2];    // B of layer 1: [128][96]
+  unsigned char W2[HID * HID * 2];    // [128][128]
+  unsigned char W3[HID * HID * 2];
+  unsigned char W4[OUTP * HID * 2];   // [32][128]
+  unsigned char A0[TM * HID * 2];     // X (K = 96), then H2 (K = 128)
+  unsigned char A1[TM * HID * 2];     // H1, H3 (K = 128)
+  float bias[3 * HID + OUTP];
+  unsigned long long bar_w, bar_mma;
+  uint32_t taddr;
+};
+constexpr uint32_t WBYTES = HID * INP * 2 + 2 * HID * HID * 2 + OUTP * HID * 2;
+
+// shared-memory matrix descriptor: start address, leading byte offset
+// (between core matrices along K: 128), stride byte offset (between 8-row
+// groups: K/8 core matrices of 128 bytes), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(const void* p, int K) {
+  const uint64_t a = smem_u32(p), lbo = 128, sbo = (uint64_t)(K / 8) * 128;
+  return ((a >> 4) & 0x3FFFull) | (((lbo >> 4) & 0x3FFFull) << 16) | (((sbo >> 4) & 0x3FFFull) << 32) |
+         (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id, int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(id), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// bounded wait on the phase with the given parity; false after WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long i = 0; i < WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// bulk asynchronous global -> shared copy (16-byte aligned, size a multiple
+// of 16) completing `bytes` transactions on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's accumulator lane, waited on
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// one layer: D [128 x N] = A [128 x K] B^T, B stored [N][K]; K / 16 MMAs,
+// each advancing both descriptors by two core matrices (256 bytes) along K
+__device__ __forceinline__ void layer_mma(uint32_t tmem, const unsigned char* A, const unsigned char* B, int K,
+                                          int N) {
+  const uint32_t id = idesc_bf16(N);
+  for (int k = 0; k < K / 16; ++k) mma_bf16(tmem, sdesc(A + k * 256, K), sdesc(B + k * 256, K), id, k > 0);
+}
+
+// bias + GELU of the accumulator row of this thread into the next layer's A
+// operand (K = 128, canonical layout)
+__device__ __forceinline__ void hidden_rows(uint32_t trow, const float* b, unsigned char* An, int r) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < HID; c0 += 32) {
+    float v[32];
+    tmem_ld32(trow + (uint32_t)c0, v);
+#pragma unroll
+    for (int j8 = 0; j8 < 4; ++j8) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 8 * j8 + 2 * q;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu(v[8 * j8 + 2 * q] + b[c]), gelu(v[8 * j8 + 2 * q + 1] + b[c + 1]));
+        pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      *reinterpret_cast<uint4*>(An + coff(r, c0 + 8 * j8, HID)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TTHREADS, 1)
+    k_mlp_fwd_tc(const bf16* __restrict__ X, float* __restrict__ Y, const unsigned char* __restrict__ Wc, Dev w,
+                 int nout, int64_t M, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  Smem& s = *reinterpret_cast<Smem*>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.taddr)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&s.bar_w, 1);
+    mbar_init(&s.bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < HID; i += TTHREADS) {
+    s.bias[i] = w.b1[i];
+    s.bias[HID + i] = w.b2[i];
+    s.bias[2 * HID + i] = w.b3[i];
+  }
+  if (tid < OUTP) s.bias[3 * HID + tid] = w.b4[tid];
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s.taddr;
+  if (tid == 0) {
+    mbar_expect_tx(&s.bar_w, WBYTES);
+    bulk_g2s(s.W1, Wc, HID * INP * 2, &s.bar_w);
+    bulk_g2s(s.W2, Wc + HID * INP * 2, HID * HID * 2, &s.bar_w);
+    bulk_g2s(s.W3, Wc + HID * INP * 2 + HID * HID * 2, HID * HID * 2, &s.bar_w);
+    bulk_g2s(s.W4, Wc + HID * INP * 2 + 2 * HID * HID * 2, OUTP * HID * 2, &s.bar_w);
+  }
+  bool ok = __syncthreads_and(mbar_wait(&s.bar_w, 0));
+  uint32_t phase = 0;
+  const int r = warp * 32 + lane;                              // this thread's row of the tile
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // its warp's accumulator lanes
+  const int64_t ntiles = (M + TM - 1) / TM;
+  const unsigned char* Wl[4] = {s.W1, s.W2, s.W3, s.W4};
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row0 = t * TM;
+    for (int i = tid; i < TM * (INP / 8); i += TTHREADS) {
+      const int rr = i / (INP / 8), c = i % (INP / 8);
+      int4 v = make_int4(0, 0, 0, 0);
+      if (row0 + rr < M) v = reinterpret_cast<const int4*>(X + (row0 + rr) * INP)[c];
+      *reinterpret_cast<int4*>(s.A0 + coff(rr, 8 * c, INP)) = v;
+    }
+    fence_async_smem();
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 0; l < 4; ++l) {
+      const unsigned char* A = (l & 1) ? s.A1 : s.A0;
+      unsigned char* An = (l & 1) ? s.A0 : s.A1;
+      if (tid == 0 && ok) {
+        fence_after();
+        layer_mma(tmem, A, Wl[l], l == 0 ? INP : HID, l == 3 ? OUTP : HID);
+        mma_commit(&s.bar_mma);
+      }
+      const bool done = ok ? mbar_wait(&s.bar_mma, phase) : false;
+      phase ^= 1;
+      ok = __syncthreads_and(done);
+      fence_after();
+      if (l < 3) {
+        if (ok) hidden_rows(trow, s.bias + l * HID, An, r);
+      } else {
+        const int64_t gr = row0 + r;
+        float v[32];
+        if (ok) tmem_ld32(trow, v);
+        if (gr < M) {
+#pragma unroll
+          for (int j = 0; j < OUTP; ++j)
+            if (j < nout) Y[gr * nout + j] = ok ? v[j] + s.bias[3 * HID + j] : __int_as_float(0x7fc00000);
+        }
+      }
+      fence_before();
+      fence_async_smem();
+      __syncthreads();
+    }
+  }
+  if (!ok && tid == 0) *err = 1;
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// the four weight matrices, BF16, transposed ([N][K]), in the canonical
+// layout of k_mlp_fwd_tc: W1 [128][96], W2, W3 [128][128], W4 [32][128]
+__global__ void k_pack_tc(const float* __restrict__ theta, int nin, int nout, unsigned char* __restrict__ Wc) {
+  const int oW2 = nin * HID + HID, oW3 = oW2 + HID * HID + HID, oW4 = oW3 + HID * HID + HID;
+  const int n1 = HID * INP, n2 = HID * HID, n4 = OUTP * HID;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n1 + 2 * n2 + n4; t += gridDim.x * blockDim.x) {
+    float v;
+    unsigned char* dst;
+    if (t < n1) {
+      const int n = t / INP, k = t % INP;
+      v = k < nin ? theta[k * HID + n] : 0.f;
+      dst = Wc + coff(n, k, INP);
+    } else if (t < n1 + 2 * n2) {
+      const int u = (t - n1) % n2, n = u / HID, k = u % HID;
+      const bool second = t >= n1 + n2;
+      v = theta[(second ? oW3 : oW2) + k * HID + n];
+      dst = Wc + n1 * 2 + (second ? n2 * 2 : 0) + coff(n, k, HID);
+    } else {
+      const int u = t - n1 - 2 * n2, n = u / HID, k = u % HID;
+      v = n < nout ? theta[oW4 + k * nout + n] : 0.f;
+      dst = Wc + (n1 + 2 * n2) * 2 + coff(n, k, HID);
+    }
+    *reinterpret_cast<bf16*>(dst) = __float2bfloat16(v);
+  }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
 // line features / targets / prediction (direction-1 lines)
 // ---------------------------------------------------------------------------
 __global__ void k_features(const double* __restrict__ Un, const double* __restrict__ Um1,
@@ -491,6 +758,8 @@ struct ldg_mlp {
   float *mean = nullptr, *rstd = nullptr, *oscale = nullptr;
   float* slots = nullptr;
   int64_t slot_cap = 0;
+  unsigned char* Wc = nullptr;  // weights in the canonical layout of the tcgen05 forward
+  int* err = nullptr;           // set by a forward whose waits ran out (outputs NaN)
   bf16* Xbuf = nullptr;  // prediction workspace
   float* Ybuf = nullptr;
   int64_t pred_cap = 0;
@@ -512,14 +781,16 @@ static int pack(ldg_mlp_t* m, cudaStream_t st) {
   const int n = HID * LDH > HID * LDX ? HID * LDH : HID * LDX;
   k_pack<<<(n + 255) / 256, 256, 0, st>>>(m->theta, m->nin, m->nout, m->W1t, m->W2t, m->W3t, m->W4t, m->b1,
                                          m->b2, m->b3, m->b4);
-  count_launch();
+  tc::k_pack_tc<<<128, 256, 0, st>>>(m->theta, m->nin, m->nout, m->Wc);
+  count_launch(2);
   return cudaGetLastError() == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
 }
 
 extern "C" int ldg_mlp_destroy(ldg_mlp_t* m) {
   if (!m) return LDG_OK;
   void* ptrs[] = {m->theta, m->m,  m->v,  m->grad, m->W1t, m->W2t,  m->W3t,   m->W4t, m->b1,
-                  m->b2,    m->b3, m->b4, m->mean, m->rstd, m->oscale, m->slots, m->Xbuf, m->Ybuf};
+                  m->b2,    m->b3, m->b4, m->mean, m->rstd, m->oscale, m->slots, m->Xbuf, m->Ybuf,
+                  m->Wc,    m->err};
   for (void* p : ptrs) cudaFree(p);
   delete m;
   return LDG_OK;
@@ -551,6 +822,8 @@ extern "C" int ldg_mlp_create(int32_t n_in, int32_t n_out, ldg_mlp_t** out) {
   al((void**)&m->mean, INP * 4);
   al((void**)&m->rstd, INP * 4);
   al((void**)&m->oscale, OUTP * 4);
+  al((void**)&m->Wc, tc::WBYTES);
+  al((void**)&m->err, sizeof(int));
   if (e != cudaSuccess) {
     ldg_mlp_destroy(m);
     return LDG_ERR_CUDA;
@@ -600,13 +873,18 @@ static cudaError_t smem_attr(const void* kern) {
   return ldg::smem_attr_cached(kern, sizeof(Smem));
 }
 
+// inference: the tcgen05 forward, one persistent CTA per SM at most
 extern "C" int ldg_mlp_forward(ldg_mlp_t* m, const void* X, int64_t M, float* Y, void* stream) {
   if (!m || !X || !Y || M < 0) return LDG_ERR_ARG;
   if (M == 0) return LDG_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  if (smem_attr((const void*)k_mlp<false>) != cudaSuccess) return LDG_ERR_CUDA;
-  k_mlp<false><<<(unsigned)((M + TR - 1) / TR), THREADS, sizeof(Smem), st>>>(
-      (const bf16*)X, nullptr, Y, m->dev(), m->nin, m->nout, M, 0.f, nullptr, 0);
+  if (ldg::smem_attr_cached((const void*)tc::k_mlp_fwd_tc, sizeof(tc::Smem)) != cudaSuccess) return LDG_ERR_CUDA;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LDG_ERR_CUDA;
+  const int64_t tiles = (M + tc::TM - 1) / tc::TM;
+  tc::k_mlp_fwd_tc<<<(unsigned)(tiles < sms ? tiles : sms), tc::TTHREADS, sizeof(tc::Smem), st>>>(
+      (const bf16*)X, Y, m->Wc, m->dev(), m->nout, M, m->err);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? LDG_OK : LDG_ERR_CUDA;
 }

@@ -163,3 +163,27 @@ def test_line_features_targets_and_predict(L):
     L.ldg_mlp_forward(mlp, X, Y)
     ref = M.scatter_correction(Y.cpu().numpy().astype(np.float64) * oscale, U[2], U[1], 3, 3)
     assert np.abs(U0.cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("rows", [1, 127, 128, 300, 5000])
+def test_tensor_memory_forward_matches_training_forward(L, rows):
+    # inference runs on tcgen05 (tensor-memory accumulators, 128-line tiles),
+    # training's forward on the warp-level MMAs; both round the same values to
+    # BF16 at the same points, so with the inference outputs as targets the
+    # training kernel's loss mean((Y_train - Y_inf)^2) holds only FP32
+    # accumulation order and the rare BF16 activation that rounds the other way
+    # (a wrong operand layout gives O(1)); ragged tiles (1, 127, 300 rows) and
+    # several tiles per CTA
+    import torch
+    theta, X, _ = _rand_problem(M_rows=rows, seed=11)
+    m = L.ldg_mlp_create(69, 20)
+    L.ldg_mlp_params(m, theta)
+    Y = torch.full((rows, 20), float("nan"), dtype=torch.float32, device="cuda")
+    L.ldg_mlp_forward(m, _xt(X), Y)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Y).all()
+    g = torch.empty(M.n_params(69, 20), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    L.ldg_mlp_grad(m, _xt(X), Y, g, loss)
+    torch.cuda.synchronize()
+    assert float(loss) <= 1e-6 * float((Y * Y).mean()), (float(loss), float((Y * Y).mean()))
