@@ -108,11 +108,11 @@ def euler_residual_flops(D, p, nc, E):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the timed kernels from one ncu capture of the unchanged kernel on this
-# workload (for the Gram-Schmidt sweeps, whose size varies with the basis:
-# the mean over every launch of one timed step); None until a capture of the
-# current kernel exists.
-TRAFFIC = {"precond_apply": 125.28e6, "jacvec": None, "gram_schmidt": 37.28e6}
+# the timed kernels from one ncu capture of the unchanged kernels on this
+# workload, every launch of one timed FP64 step (for the Gram-Schmidt
+# sweeps, whose size varies with the basis: the mean over their launches);
+# set to None when a kernel changes until it is captured again.
+TRAFFIC = {"precond_apply": 121.47e6, "jacvec": 188.40e6, "gram_schmidt": 37.28e6}
 
 
 def jac_bytes(h, esz):
@@ -234,6 +234,8 @@ def gpu_arm(args):
     dt = 0.05
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    timed_launches = {}   # library kernel launches inside the timed steps, per mode
+
     def run(mode, K, W, e2e=False, live=False):
         """W warm-up + K timed BDF2 levels; returns per-step ms and stats.
         With live=True the apply and matvec launches of the K timed levels
@@ -248,11 +250,13 @@ def gpu_arm(args):
             hostbuf[0].copy_(Un.view(-1).cpu())
             hostbuf[1].copy_(Unm1.view(-1).cpu())
         times, stats = [], []
+        timed_launches[mode] = 0
         for it in range(W + K):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             Unext = torch.empty_like(Un)
+            l0 = ldg.ldg_launch_count()
             e0.record(st)
             if e2e:
                 Un_d = torch.empty_like(Un)
@@ -273,6 +277,7 @@ def gpu_arm(args):
             if it >= W:
                 times.append(e0.elapsed_time(e1))
                 stats.append(s)
+                timed_launches[mode] += ldg.ldg_launch_count() - l0
             if e2e:
                 hostbuf[0], hostbuf[1], hostbuf[2] = hostbuf[2], hostbuf[0], hostbuf[1]
             else:
@@ -302,13 +307,12 @@ def gpu_arm(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
-    l0 = ldg.ldg_launch_count()
     t64, s64 = run(ldg.MODE_FP64, args.steps, args.warmup)
-    launches = (ldg.ldg_launch_count() - l0)
+    launches = timed_launches[ldg.MODE_FP64]
     clocks = clk.stop()
     torch.cuda.synchronize()
     ms, value = job_rate(np.mean(t64), h.ndof, ws, "cuda")
-    launches_per_step = launches / (args.steps + args.warmup + 1)
+    launches_per_step = launches / args.steps
     # the same steps again with every apply, matvec and Gram-Schmidt launch
     # bracketed by CUDA events on its stream (the brackets cost about 1 ms a
     # step, so these steps are not the ones `value` is taken from): device
@@ -401,7 +405,7 @@ def gpu_arm(args):
     # time from the live CUDA events; the bound is the roofline it is closer to.
     names = {"precond_apply": "k_precond_apply (element ILU(0) apply, FP64)",
              "jacvec": "k_jacvec (split matvec K11 x, FP64)",
-             "gram_schmidt": "k_ortho (fused CGS2 sweeps of GMRES, FP64)"}
+             "gram_schmidt": "k_ortho (fused classical Gram-Schmidt sweeps of GMRES, FP64)"}
     per_kernel = {}
     for kname, (n_l, ms_l, by_l, fl_l) in live.items():
         if n_l == 0 or ms_l <= 0:
@@ -431,16 +435,19 @@ def gpu_arm(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": h.E, "p": h.p, "dof": h.ndof,
-                   "newton_rtol": 1e-8, "linear": "GMRES(30) + element-block ILU(0), eta=1e-3",
+                   "newton_rtol": 1e-8, "linear": "GMRES(30) + element-block ILU(0), eta=1e-3, classical Gram-Schmidt with "
+                             "a second pass where one shrinks the column more than 10x",
                    "jacobian": "rebuilt every step", "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{ws}"},
         "newton_its": float(np.mean([s["newton_its"] for s in s64])),
         "gmres_its": float(np.mean([s["gmres_its"] for s in s64])),
+        "reorth_its": float(np.mean([s["reorth_its"] for s in s64])),
         "phases_ms_fp64": ph,
         "mixed": {"ms_per_step": ms_mx, "value": value_mx,
                   "speedup_vs_fp64": ms / ms_mx,
                   "newton_its": float(np.mean([s["newton_its"] for s in smx])),
                   "gmres_its": float(np.mean([s["gmres_its"] for s in smx])),
+                  "reorth_its": float(np.mean([s["reorth_its"] for s in smx])),
                   "phases_ms": {k: float(np.mean([s[k] for s in smx])) for k in ph}},
         "kernels": kernels,
         "dirk3": dict(dirk, note="one step of the paper's three-stage DIRK on the same workload and dt, "
@@ -450,7 +457,7 @@ def gpu_arm(args):
         "fp64_peak": dict(fp64pk, nominal_tflops=FP64_NOMINAL_TFLOPS),
         "e2e": {"value": value_e2e, "unit": "DOF/s",
                 "h2d_bytes_per_step": 2 * h.ndof * 8, "d2h_bytes_per_step": h.ndof * 8},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches,
         "gpu_launches_per_step": launches_per_step,
         "clocks": clocks,
     }
@@ -590,7 +597,8 @@ def channel_section(args, hbm):
     adiabatic), 64 x 32 x 32 curved hexes with wall-normal stretching 1.1,
     p = 4 (41M DOF), Re = 5000, Mach 0.3: the kernels at full size, then one
     BDF2 level at CFL 50 (dt from the smallest node spacing and |u| + c) in
-    mixed precision and in FP64 from the same BDF1 start level."""
+    mixed precision and in FP64 from the same BDF1 start level (--channel-steps
+    levels each, --channel-forcing of the linear solves)."""
     import numpy as np
     import torch
 
@@ -636,22 +644,41 @@ def channel_section(args, hbm):
     torch.cuda.empty_cache()
     Un = torch.from_numpy(U0).cuda()
     U1 = torch.empty_like(Un)
-    s1 = ldg.ldg_newton_step(h, U1, Un, None, None, dt, ldg.solver_opts(mode=ldg.MODE_MIXED, first_step=True))
+    forcing = ldg.FORCING_TARGET if args.channel_forcing == "target" else ldg.FORCING_FIXED
+    s1 = ldg.ldg_newton_step(h, U1, Un, None, None, dt,
+                             ldg.solver_opts(mode=ldg.MODE_MIXED, first_step=True, forcing=forcing))
     out["bdf1_start"] = {"newton_its": s1["newton_its"], "gmres_its": s1["gmres_its"]}
+    out["levels"] = args.channel_steps
+    out["forcing"] = args.channel_forcing
     sol = {}
     for name, mode in (("mixed", ldg.MODE_MIXED), ("fp64", ldg.MODE_FP64)):
-        U2 = torch.empty_like(Un)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        s = ldg.ldg_newton_step(h, U2, U1, Un, None, dt, ldg.solver_opts(mode=mode, force_rebuild=True))
-        e1.record()
-        e1.synchronize()
-        sol[name] = U2
-        out[name] = {"ms_per_step": e0.elapsed_time(e1), "newton_its": s["newton_its"], "gmres_its": s["gmres_its"],
-                     "res_final_rel": s["res_final"] / s["res0"],
+        # args.channel_steps BDF2 levels from the same BDF1 start, each solved
+        # to the 1e-8 target with the Jacobian rebuilt at its first iteration
+        Um1, Uc = Un, U1
+        ms, newton, gmres, res_rel = [], [], [], []
+        for _ in range(args.channel_steps):
+            U2 = torch.empty_like(Un)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s = ldg.ldg_newton_step(h, U2, Uc, Um1, None, dt,
+                                    ldg.solver_opts(mode=mode, force_rebuild=True, forcing=forcing))
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            newton.append(s["newton_its"])
+            gmres.append(s["gmres_its"])
+            res_rel.append(s["res_final"] / s["res0"])
+            if Um1 is not Un:
+                del Um1
+            Um1, Uc = Uc, U2
+        sol[name] = Uc
+        out[name] = {"ms_per_step": float(np.mean(ms)), "newton_its": float(np.mean(newton)),
+                     "gmres_its": float(np.mean(gmres)), "res_final_rel": float(np.max(res_rel)),
+                     "ms_total": float(np.sum(ms)),
                      "phases_ms": {q: s[q] for q in ("t_residual_ms", "t_jacobian_ms", "t_precond_ms",
                                                      "t_linear_ms")}}
+        del Um1
         torch.cuda.empty_cache()
     out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     out["rel_diff_mixed_vs_fp64"] = float((sol["mixed"] - sol["fp64"]).norm() / sol["fp64"].norm())
@@ -911,6 +938,8 @@ def main():
     ap.add_argument("--channel", type=int, nargs=3, default=[64, 32, 32])
     ap.add_argument("--no-stabilized", action="store_true", help="skip the stabilised-LDG Poisson section")
     ap.add_argument("--channel-cfl", type=float, default=50.0)
+    ap.add_argument("--channel-steps", type=int, default=1, help="BDF2 levels of the channel per precision")
+    ap.add_argument("--channel-forcing", default="fixed", choices=["fixed", "target"])
     ap.add_argument("--learn-n", type=int, default=16)
     ap.add_argument("--learn-dt", type=float, default=0.03)
     ap.add_argument("--learn-traj", type=int, default=200)

@@ -344,7 +344,16 @@ typedef struct {
                             halve ||G|| (an addition to the paper's policy)   */
   int32_t forcing;       /* LDG_FORCING_*: relative tolerance of each linear
                             solve (not in the paper)                          */
+  int32_t ortho;         /* LDG_ORTHO_*: Gram-Schmidt of the Arnoldi columns
+                            (the paper does not name one)                     */
 } ldg_solver_opts_t;
+
+#define LDG_ORTHO_CGS2 0      /* classical Gram-Schmidt, always twice          */
+#define LDG_ORTHO_SELECTIVE 1 /* FP64 basis: classical Gram-Schmidt, a second
+                                 pass only where the first shrank the column
+                                 by more than a factor 10 (Rutishauser's
+                                 criterion); an FP32 basis (LDG_MODE_MIXED)
+                                 always takes CGS2                            */
 
 #define LDG_FORCING_FIXED 0  /* every linear solve to gmres_tol ||G||          */
 #define LDG_FORCING_TARGET 1 /* to max(gmres_tol, 0.5 target / ||G||) ||G||
@@ -367,6 +376,8 @@ typedef struct {
   double t_linear_ms;
   double res_extrap;     /* ||G|| of the extrapolation (LDG_PRED_CHECKED)     */
   double pred_weight;    /* weight b of the caller's guess (LDG_PRED_CHECKED) */
+  int32_t reorth_its;    /* GMRES iterations whose Arnoldi column took a
+                            second Gram-Schmidt pass                          */
 } ldg_step_stats_t;
 
 /*

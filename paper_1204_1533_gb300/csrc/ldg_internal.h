@@ -78,18 +78,22 @@ struct Geo {
   int64_t E;
 };
 
-// Arnoldi column of GMRES by CGS2 (ldg_ortho.cu): orthogonalises w against
-// the kv basis vectors Vb[0..kv) (stride n) and normalises it. Device
-// scratch: part [GS_PART_LEN], gs [GS_SCRATCH_LEN] doubles. Host col
-// [2 kv + 2]: on return col[0..kv) = Hessenberg entries, col[kv] = the norm
-// before normalisation (0: w lies in the span). Synchronises on st.
+// Arnoldi column of GMRES by CGS2, or with selective = true by classical
+// Gram-Schmidt re-orthogonalised only where one pass shrank w by more than
+// a factor 10 (ldg_ortho.cu): orthogonalises w against the kv basis vectors
+// Vb[0..kv) (stride n) and normalises it. Device scratch: part
+// [GS_PART_LEN], gs [GS_SCRATCH_LEN] doubles. Host col [2 kv + 2]: on
+// return col[0..kv) = Hessenberg entries, col[kv] = the norm before
+// normalisation (0: w lies in the span); *passes (if not null) = the
+// Gram-Schmidt passes made (1 or 2). Synchronises on st.
 constexpr int GS_KMAX = 32;        // basis vectors per fused sweep
 constexpr int GS_MAX_BASIS = 66;   // largest basis (restart 64 + 2)
 constexpr int GS_MAX_BLOCKS = 320;
 constexpr size_t GS_PART_LEN = (size_t)(GS_KMAX + 1) * GS_MAX_BLOCKS;
 constexpr size_t GS_SCRATCH_LEN = 4 * (GS_MAX_BASIS + 2);
 template <typename V>
-int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, cudaStream_t st);
+int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, bool selective,
+                   int* passes, cudaStream_t st);
 
 cudaError_t launch_gradient(const struct ::ldg_handle* h, const double* U, double* Q,
                             cudaStream_t st);
@@ -175,6 +179,8 @@ struct ldg_jac {
   void* Kw = nullptr;     // wall ends: energy row of the wall-state derivative, 2 n_c per line (tiles)
   void* gbuf = nullptr;   // K21 x workspace [E][nc][D][npe] in the vector precision (double)
   void* ucvt = nullptr;   // FP32 Jacobians: FP32 copies of U [ndof] and Q [ndof D] for the assembly
+  void* geof = nullptr;   // FP32 Jacobians: FP32 copies of ng, nend, invJ (made at the first build)
+  bool geof_ready = false;
 };
 
 // Element-block ILU(0) factors [E][npe][Dp+1][nc][nc] at the Jacobian's

@@ -83,9 +83,8 @@ __device__ __forceinline__ int64_t tile_index(int64_t L, int64_t nk, int64_t k) 
 //     dr_i/du_j = -sum_q Kd_iq phi_j(xi_q) A_q + L_end,i B_end,in [j = end]
 //   and the store; a warp covers the 32 lines of the tile for one entry, so
 //   every store is one 128-byte (FP32) segment.
-// The state and gradient arrive at the arithmetic precision R (FP32 copies
-// for the FP32 Jacobian), so the derivative arithmetic is pure R; only the
-// metric terms are converted, once per use.
+// The state, gradient and metric terms arrive at the arithmetic precision R
+// (FP32 copies for the FP32 Jacobian), so the assembly is pure R.
 // ---------------------------------------------------------------------------
 template <typename R, int M>
 __device__ __forceinline__ Dual<R, M> dseed(R v, int k) {
@@ -102,12 +101,25 @@ __device__ __forceinline__ Dual<R, M> dconst(R v) {
   return x;
 }
 
+// metric terms at the arithmetic precision R (FP32 copies made once per
+// FP32 Jacobian object; the FP64 arrays themselves for R = double)
+template <typename R>
+struct GeoR {
+  const R* ng;    // [E][D][nl][nq][D]
+  const R* nend;  // [E][D][nl][2][D]
+  const R* invJ;  // [E][npe]
+};
+
 template <int D, int P, int NC, int EQ, typename R>
 struct JacTile {
   using S = Shape<D, P>;
   static constexpr int N = S::N, NQ = S::NQ, NPE = S::NPE, NL = S::NL, NCD = NC * D;
   static constexpr bool VISC = IsViscous<EQ>::value;
-  static constexpr int KINDS = NQ + 2;  // phase-A item kinds per line: Gauss points, two ends
+  // phase-A item kinds per line: K11 round: the four (end, side) face-flux
+  // derivatives first (the heaviest items, one per warp of the block), then
+  // the Gauss points; K12 round: the Gauss points and the two ends
+  static constexpr int KINDS11 = 4 + NQ;
+  static constexpr int KINDS12 = NQ + 2;
   // four warps per block and two blocks per SM: the derivative arithmetic
   // needs up to 255 registers a thread, and two blocks with their own
   // barriers let one block's stores overlap the other's arithmetic
@@ -218,7 +230,7 @@ __device__ __forceinline__ void end_flux_derivative(const R* uin, const R* uo, c
 template <int D, int P, int NC, int EQ, typename R, int ROUND>
 __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROUND>(), (JacTile<D, P, NC, EQ, R>::MINB))
     k_jacobian(const R* __restrict__ Ur, const R* __restrict__ Qr, R* __restrict__ K11, R* __restrict__ K12,
-               R* __restrict__ Kw, Geo g, Tab tab, PhysArgs ph, int64_t nlines) {
+               R* __restrict__ Kw, Geo g, GeoR<R> gr, Tab tab, PhysArgs ph, int64_t nlines) {
   using JT = JacTile<D, P, NC, EQ, R>;
   using S = Shape<D, P>;
   constexpr int N = JT::N, NQ = JT::NQ, NPE = JT::NPE, NCD = JT::NCD;
@@ -234,17 +246,17 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
   if constexpr (ROUND == 1) {
   R* A = sm;                         // [NQ][NC][NC][32]
   R* B = sm + NQ * NC * NC * 32;     // [end][side][NC][NC][32]
-  for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::template threads<ROUND>()) {
+  for (int it = threadIdx.x; it < 32 * JT::KINDS11; it += JT::template threads<ROUND>()) {
     const int lane = it & 31, kind = it >> 5;
     const int64_t L = tile0 + lane;
     if (L >= nlines) continue;
     const LineAt<D, P> ln(L);
     const R* ue = Ur + ln.e * NC * NPE;
-    if (kind < NQ) {
-      const int q = kind;
+    if (kind >= 4) {
+      const int q = kind - 4;
       R n[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) n[a] = (R)g.ng[(L * NQ + q) * D + a];
+      for (int a = 0; a < D; ++a) n[a] = gr.ng[(L * NQ + q) * D + a];
       using T = Dual<R, NC>;
       T uq[NC], f[NC];
 #pragma unroll
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
 #pragma unroll
         for (int cp = 0; cp < NC; ++cp) A[((q * NC + c) * NC + cp) * 32 + lane] = f[c].d[cp];
     } else {
-      const int end = kind - NQ;
+      const int end = kind >> 1, side = kind & 1;
       const int aend = ln.b0 + end * P * ln.st;
       const int nb = g.nbr[L * 2 + end];
       const int swv = g.sw[(ln.e * D + ln.d) * 2 + end];
@@ -283,7 +295,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
       R nv[D], nn = 0;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        nv[a] = (R)g.nend[(L * 2 + end) * D + a];
+        nv[a] = gr.nend[(L * 2 + end) * D + a];
         nn += nv[a] * nv[a];
       }
       nn = sqrt(nn);
@@ -316,7 +328,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
       // w = (|m|^2 / (2 rho^2), -m / rho, 1), stored per line end for the
       // K21 part of the split product
       if constexpr (VISC && NC == D + 2) {
-        if (Kw) {
+        if (Kw && side == 0) {
           R w[NC];
 #pragma unroll
           for (int c = 0; c < NC; ++c) w[c] = R(0);
@@ -335,44 +347,51 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
         }
       }
       R dF[NC * NC];
-      end_flux_derivative<D, NC, EQ, R, 0>(uin, uo, qin, qo, nv, nn, nb, swv, wall, neu, pp, dF);
+      if (side == 0)
+        end_flux_derivative<D, NC, EQ, R, 0>(uin, uo, qin, qo, nv, nn, nb, swv, wall, neu, pp, dF);
+      else
+        end_flux_derivative<D, NC, EQ, R, 1>(uin, uo, qin, qo, nv, nn, nb, swv, wall, neu, pp, dF);
 #pragma unroll
-      for (int k = 0; k < NC * NC; ++k) B[((end * 2 + 0) * NC * NC + k) * 32 + lane] = dF[k];
-      end_flux_derivative<D, NC, EQ, R, 1>(uin, uo, qin, qo, nv, nn, nb, swv, wall, neu, pp, dF);
-#pragma unroll
-      for (int k = 0; k < NC * NC; ++k) B[((end * 2 + 1) * NC * NC + k) * 32 + lane] = dF[k];
+      for (int k = 0; k < NC * NC; ++k) B[((end * 2 + side) * NC * NC + k) * 32 + lane] = dF[k];
     }
   }
   __syncthreads();
-  // phase B: row i, block column jj (in-line j < N, face blocks N, N + 1)
-  for (int it = threadIdx.x; it < 32 * N * (N + 2); it += JT::template threads<ROUND>()) {
-    const int lane = it & 31, r = it >> 5;
-    const int i = r / (N + 2), jj = r % (N + 2);
+  // phase B: warp w takes the entries k = w, w + warps, ... of each row i;
+  // per entry it reads the NQ + 4 pointwise values once and writes the N
+  // in-line blocks and the two face blocks of the row (32 lines: one
+  // 128-byte FP32 segment per store)
+  {
+    constexpr int NW = JT::template threads<ROUND>() / 32;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int64_t L = tile0 + lane;
-    if (L >= nlines) continue;
-    const LineAt<D, P> ln(L);
-    const R ij = (R)g.invJ[ln.e * NPE + ln.b0 + i * ln.st];
-    if (jj < N) {
-      const int j = jj;
-      R w[NQ];
+    const bool live = L < nlines;
+    const LineAt<D, P> ln(live ? L : tile0);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) w[q] = kdphi<R>(tab, i, q, j);
-      const R l0 = (j == 0) ? tlift<R>(tab, 0, i) : R(0);
-      const R l1 = (j == P) ? tlift<R>(tab, 1, i) : R(0);
+    for (int i = 0; i < N; ++i) {
+      R w[NQ][N];
 #pragma unroll
-      for (int k = 0; k < NC * NC; ++k) {
-        R s = l0 * B[((0 * 2 + 0) * NC * NC + k) * 32 + lane] + l1 * B[((1 * 2 + 0) * NC * NC + k) * 32 + lane];
+      for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) s -= w[q] * A[(q * NC * NC + k) * 32 + lane];
-        K11[tile_index(L, JT::NK11, (i * N + j) * NC * NC + k)] = -ij * s;
+        for (int j = 0; j < N; ++j) w[q][j] = kdphi<R>(tab, i, q, j);
+      const R l0 = tlift<R>(tab, 0, i), l1 = tlift<R>(tab, 1, i);
+      const R ij = live ? gr.invJ[ln.e * NPE + ln.b0 + i * ln.st] : R(0);
+      for (int k = wp; k < NC * NC; k += NW) {
+        R a[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q] = A[(q * NC * NC + k) * 32 + lane];
+        const R b00 = B[((0 * 2 + 0) * NC * NC + k) * 32 + lane], b10 = B[((1 * 2 + 0) * NC * NC + k) * 32 + lane];
+        const R b01 = B[((0 * 2 + 1) * NC * NC + k) * 32 + lane], b11 = B[((1 * 2 + 1) * NC * NC + k) * 32 + lane];
+        if (!live) continue;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          R s = (j == 0 ? l0 * b00 : R(0)) + (j == P ? l1 * b10 : R(0));
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) s -= w[q][j] * a[q];
+          K11[tile_index(L, JT::NK11, (i * N + j) * NC * NC + k)] = -ij * s;
+        }
+        K11[tile_index(L, JT::NK11, JT::OFF11 + (0 * N + i) * NC * NC + k)] = -ij * l0 * b01;
+        K11[tile_index(L, JT::NK11, JT::OFF11 + (1 * N + i) * NC * NC + k)] = -ij * l1 * b11;
       }
-    } else {
-      const int end = jj - N;
-      const R li = tlift<R>(tab, end, i);
-#pragma unroll
-      for (int k = 0; k < NC * NC; ++k)
-        K11[tile_index(L, JT::NK11, JT::OFF11 + (end * N + i) * NC * NC + k)] =
-            -ij * li * B[((end * 2 + 1) * NC * NC + k) * 32 + lane];
     }
   }
 
@@ -382,7 +401,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
     R* A2 = sm;                            // [NQ][NC][NCD][32]
     R* C2 = sm + NQ * NC * NCD * 32;       // [end][NC][NCD][32] in-line end terms
     R* Cf = C2 + 2 * NC * NCD * 32;        // [NC][NCD][32] face block
-    for (int it = threadIdx.x; it < 32 * JT::KINDS; it += JT::template threads<ROUND>()) {
+    for (int it = threadIdx.x; it < 32 * JT::KINDS12; it += JT::template threads<ROUND>()) {
       const int lane = it & 31, kind = it >> 5;
       const int64_t L = tile0 + lane;
       if (L >= nlines) continue;
@@ -392,7 +411,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
         const int q = kind;
         R n[D], uq[NC];
 #pragma unroll
-        for (int a = 0; a < D; ++a) n[a] = (R)g.ng[(L * NQ + q) * D + a];
+        for (int a = 0; a < D; ++a) n[a] = gr.ng[(L * NQ + q) * D + a];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           R s = 0;
@@ -419,7 +438,7 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
         const bool outside = nb >= 0 && swv == 1;
         R nv[D], ut[NC];
 #pragma unroll
-        for (int a = 0; a < D; ++a) nv[a] = (R)g.nend[(L * 2 + end) * D + a];
+        for (int a = 0; a < D; ++a) nv[a] = gr.nend[(L * 2 + end) * D + a];
         if (outside) {
           const int64_t eo = nb / NPE;
           const int ao = nb % NPE;
@@ -460,40 +479,48 @@ __global__ void __launch_bounds__(JacTile<D, P, NC, EQ, R>::template threads<ROU
       }
     }
     __syncthreads();
-    // phase B: row i, block column jj (in-line j < N, the face block N)
-    for (int it = threadIdx.x; it < 32 * N * (N + 1); it += JT::template threads<ROUND>()) {
-      const int lane = it & 31, r = it >> 5;
-      const int i = r / (N + 1), jj = r % (N + 1);
+    // phase B: as in the K11 round, warp w takes entries k = w, w + warps,
+    // ... of each row i: NQ + 3 reads, N + 1 stores
+    {
+      constexpr int NW = JT::template threads<ROUND>() / 32;
+      const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
       const int64_t L = tile0 + lane;
-      if (L >= nlines) continue;
-      const LineAt<D, P> ln(L);
-      const R ij = (R)g.invJ[ln.e * NPE + ln.b0 + i * ln.st];
-      if (jj < N) {
-        const int j = jj;
-        R w[NQ];
+      const bool live = L < nlines;
+      const LineAt<D, P> ln(live ? L : tile0);
+      const int fe = live ? fend[lane] : 0;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) w[q] = kdphi<R>(tab, i, q, j);
-        const R l0 = (j == 0) ? tlift<R>(tab, 0, i) : R(0);
-        const R l1 = (j == P) ? tlift<R>(tab, 1, i) : R(0);
-#pragma unroll 5
-        for (int k = 0; k < NC * NCD; ++k) {
-          R s = l0 * C2[(0 * NC * NCD + k) * 32 + lane] + l1 * C2[(1 * NC * NCD + k) * 32 + lane];
+      for (int i = 0; i < N; ++i) {
+        R w[NQ][N];
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) s -= w[q] * A2[(q * NC * NCD + k) * 32 + lane];
-          K12[tile_index(L, JT::NK12, (i * N + j) * NC * NCD + k)] = -ij * s;
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int j = 0; j < N; ++j) w[q][j] = kdphi<R>(tab, i, q, j);
+        const R l0 = tlift<R>(tab, 0, i), l1 = tlift<R>(tab, 1, i), li = tlift<R>(tab, fe, i);
+        const R ij = live ? gr.invJ[ln.e * NPE + ln.b0 + i * ln.st] : R(0);
+        for (int k = wp; k < NC * NCD; k += NW) {
+          R a[NQ];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) a[q] = A2[(q * NC * NCD + k) * 32 + lane];
+          const R c0 = C2[(0 * NC * NCD + k) * 32 + lane], c1 = C2[(1 * NC * NCD + k) * 32 + lane];
+          const R cf = Cf[k * 32 + lane];
+          if (!live) continue;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            R s = (j == 0 ? l0 * c0 : R(0)) + (j == P ? l1 * c1 : R(0));
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) s -= w[q][j] * a[q];
+            K12[tile_index(L, JT::NK12, (i * N + j) * NC * NCD + k)] = -ij * s;
+          }
+          K12[tile_index(L, JT::NK12, JT::OFF12 + i * NC * NCD + k)] = -ij * li * cf;
         }
-      } else {
-        const R li = tlift<R>(tab, fend[lane], i);
-#pragma unroll 5
-        for (int k = 0; k < NC * NCD; ++k)
-          K12[tile_index(L, JT::NK12, JT::OFF12 + i * NC * NCD + k)] = -ij * li * Cf[k * 32 + lane];
       }
     }
   }
 }
 
 template <int D, int P, int EQ, typename R>
-cudaError_t run_jacobian(const ldg_handle* h, const R* Ur, const R* Qr, R* K11, R* K12, R* Kw, cudaStream_t st) {
+cudaError_t run_jacobian(const ldg_handle* h, const R* Ur, const R* Qr, R* K11, R* K12, R* Kw, GeoR<R> gr,
+                         cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
   using JT = JacTile<D, P, NC, EQ, R>;
   constexpr bool VISC = IsViscous<EQ>::value;
@@ -505,8 +532,8 @@ cudaError_t run_jacobian(const ldg_handle* h, const R* Ur, const R* Qr, R* K11, 
     // shared memory before L1: several blocks per SM need several tile buffers
     err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)h->ntiles(), round == 1 ? JT::template threads<1>() : JT::template threads<2>(), smem, st>>>(Ur, Qr, K11, K12, Kw, h->geo(), h->tab, h->phys,
-                                                          h->nlines());
+    kern<<<(unsigned)h->ntiles(), round == 1 ? JT::template threads<1>() : JT::template threads<2>(), smem, st>>>(
+        Ur, Qr, K11, K12, Kw, h->geo(), gr, h->tab, h->phys, h->nlines());
     count_launch();
   }
   return cudaGetLastError();

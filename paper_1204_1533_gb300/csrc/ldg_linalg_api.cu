@@ -40,11 +40,22 @@ cudaError_t launch_k21(const ldg_handle* h, ldg_jac* J, cudaStream_t st) {
   LDG_DISPATCH(h, k21(h, J, st));
   return cudaErrorInvalidValue;
 }
+// algorithmic operations of the kernel timer: one multiply-add per stored
+// matrix entry (K11, K12 and each K21 entry once per component) and
+// y = shift x + scale s per unknown; ILU(0) apply: one multiply-add per
+// factor entry (the forward and backward sweeps and D^-1 together read each
+// stored block once)
+static double jacvec_flops(const ldg_handle* h) {
+  return 2.0 * (double)h->nlines() * (h->nk11() + h->nk12() + (double)h->nk21() * h->nc) + 3.0 * h->ndof;
+}
+static double apply_flops(const ldg_handle* h) {
+  return 2.0 * (double)h->E * h->npe * h->pat_w() * h->nc * h->nc;
+}
 cudaError_t launch_jacvec(const ldg_handle* h, const ldg_jac* J, double shift, double scale,
                           const void* x, void* y, int vprec, cudaStream_t st) {
   const double esz = J->prec == LDG_PREC_FP32 ? 4.0 : 8.0, vsz = vprec == LDG_PREC_FP32 ? 4.0 : 8.0;
   TimedScope tl(KT_JACVEC, vprec, st,
-                (double)h->ntiles() * 32.0 * (h->nk11() + h->nk12()) * esz + 2.0 * h->ndof * vsz, 0.0);
+                (double)h->ntiles() * 32.0 * (h->nk11() + h->nk12()) * esz + 2.0 * h->ndof * vsz, jacvec_flops(h));
   LDG_DISPATCH(h, jacvec(h, J, shift, scale, x, y, vprec, st));
   return cudaErrorInvalidValue;
 }
@@ -64,7 +75,7 @@ cudaError_t launch_precond_apply(const ldg_handle* h, const ldg_pc* P, const voi
                                  int vprec, cudaStream_t st) {
   const double esz = P->prec == LDG_PREC_FP32 ? 4.0 : 8.0, vsz = vprec == LDG_PREC_FP32 ? 4.0 : 8.0;
   TimedScope tl(KT_APPLY, vprec, st,
-                (double)h->E * h->npe * h->pat_w() * h->nc * h->nc * esz + 2.0 * h->ndof * vsz, 0.0);
+                (double)h->E * h->npe * h->pat_w() * h->nc * h->nc * esz + 2.0 * h->ndof * vsz, apply_flops(h));
   LDG_DISPATCH(h, apply(h, P, r, z, vprec, st));
   return cudaErrorInvalidValue;
 }
@@ -83,6 +94,7 @@ extern "C" int ldg_jac_destroy(ldg_jac_t* J) {
   cudaFree(J->Kw);
   cudaFree(J->gbuf);
   cudaFree(J->ucvt);
+  cudaFree(J->geof);
   delete J;
   return LDG_OK;
 }
@@ -111,6 +123,8 @@ static int jacobian_impl(ldg_handle_t* h, const double* U, const double* Qin, in
     }
     if (err == cudaSuccess && prec == LDG_PREC_FP32)
       err = cudaMalloc(&J->ucvt, (size_t)h->ndof * (h->viscous() ? 1 + h->D : 1) * sizeof(float));
+    if (err == cudaSuccess && prec == LDG_PREC_FP32)
+      err = cudaMalloc(&J->geof, ((size_t)h->nlines() * (h->nq + 2) * h->D + (size_t)h->E * h->npe) * sizeof(float));
     if (err != cudaSuccess) {
       ldg_jac_destroy(J);
       return LDG_ERR_CUDA;
@@ -197,7 +211,8 @@ extern "C" int ldg_jacvec_g(ldg_handle_t* h, const ldg_jac_t* J, double shift, d
   if (!x || !y || (h->viscous() && !g)) return LDG_ERR_ARG;
   const double esz = J->prec == LDG_PREC_FP32 ? 4.0 : 8.0, vsz = prec == LDG_PREC_FP32 ? 4.0 : 8.0;
   TimedScope tl(KT_JACVEC, prec, (cudaStream_t)stream,
-                (double)h->ntiles() * 32.0 * (h->nk11() + h->nk12()) * esz + 2.0 * h->ndof * vsz, 0.0);
+                (double)h->ntiles() * 32.0 * (h->nk11() + h->nk12()) * esz + 2.0 * h->ndof * vsz,
+                jacvec_flops(h) - 2.0 * (double)h->nlines() * h->nk21() * h->nc);
   return launch_jacvec_part(h, J, shift, scale, x, const_cast<void*>(g), y, prec, 2, (cudaStream_t)stream) ==
                  cudaSuccess
              ? LDG_OK
@@ -250,12 +265,14 @@ extern "C" int ldg_pc_export(const ldg_pc_t* P, void* factors) {
   const ldg_handle* h = P->h;
   const size_t bb = (size_t)h->nc * h->nc, W = h->pat_w(), es = esize(P->prec);
   const size_t bytes = (size_t)h->E * h->npe * W * bb * es;
-  if (cudaMemcpy(factors, P->F, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return LDG_ERR_CUDA;
+  const int N = h->p + 1;
+  if (cudaMemcpy(factors, P->F, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    return LDG_ERR_CUDA;
+  }
   // the device keeps D_i^-1 in each row's diagonal slot and U_ii aside:
   // put U_ii back (the factors as ILU(0) defines them)
   std::vector<char> ud((size_t)h->E * h->npe * bb * es);
   if (cudaMemcpy(ud.data(), P->Udiag, ud.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return LDG_ERR_CUDA;
-  const int N = h->p + 1;
   for (int64_t e = 0; e < h->E; ++e)
     for (int i = 0; i < h->npe; ++i) {
       const int dg = i % N + (i / N) % N + (h->D == 3 ? i / (N * N) : 0);  // slots of lower columns

@@ -4,7 +4,7 @@
 //   g = K21 x                        (k_k21_apply; the discrete gradient of x)
 //   y = shift x + scale (K11 x + K12 g)       (k_jacvec)
 //   A~_e = shift I + scale mask_e(K11 + K12 K21), block ILU(0)   (k_precond)
-//   z = (L U)^-1 r                   (k_precond_apply)
+//   z = (L U)^-1 r                   (k_precond_apply_lv: FP32, 3-D up to p = 3; else k_precond_apply)
 // Matrices are read at their stored precision R, vectors are V (float for
 // the mixed path, double for the FP64 path and the FP64 refinement residual),
 // sums in V. Every kernel processes whole elements per block so a line's
@@ -545,9 +545,12 @@ __global__ void __launch_bounds__(256)
 // (forward 1 .. npe-1, then backward npe-1 .. 0): lane (c, g) accumulates
 // F[i][s][c][m] y[col(s)][m] over the row's pattern slots and its m range,
 // the G lanes of component c sum their parts, and lane (c, 0) stores the
-// result in the warp's y slice (shared memory). G = n_c gives the most
-// lanes per element (for FP32, where the chain is latency-bound); G = 1
-// leaves no reduction at all (for FP64, where the FP64 pipe is the limit).
+// result in the warp's y slice (shared memory). This row-chain form serves
+// the FP64 apply, bound by the FP64 pipe (G = 1 leaves no reduction at all;
+// G = 2 doubles the warps of a small mesh; G = n_c takes element shapes too
+// large to unroll), and the FP32 apply of 2-D and p = 4 elements with
+// G = n_c (the most lanes per element); 3-D FP32 elements up to p = 3 run by
+// wavefronts (k_precond_apply_lv below).
 //
 // Row i = ix + N iy + N^2 iz couples to the nodes of its D lines; its
 // pattern slots in ascending column order are: lower z, lower y, lower x,
@@ -735,6 +738,112 @@ __global__ void __launch_bounds__(ApplyLanes<D, P, NC, G, R, V>::THREADS)
     for (int k = q; k < tile; k += A::LPE) z[e * tile + k] = y[k];
 }
 
+// ILU(0) apply by wavefronts (FP32): the rows of an element's pattern that
+// share the level ix + iy + iz are independent in both triangular solves (a
+// row's lower neighbours all lie on lower levels, its upper ones on higher
+// levels), so one warp per element takes a whole level at once, one lane
+// per (row, component): D p + 1 dependent steps per sweep instead of one per
+// row, and every lane's factor loads of a step (its row's lower or upper
+// slots, n_c values each) issued together. The backward step finishes with
+// the n_c x n_c inverse of the diagonal block, which needs the whole
+// component vector of the row: a second pass after the warp's exchange.
+template <int D, int P>
+constexpr int level_rows_max() {
+  constexpr int N = P + 1;
+  int best = 0;
+  for (int l = 0; l <= D * P; ++l) {
+    int cnt = 0;
+    for (int i = 0; i < (D == 2 ? N * N : N * N * N); ++i)
+      if (i % N + (i / N) % N + (D == 3 ? i / (N * N) : 0) == l) ++cnt;
+    best = cnt > best ? cnt : best;
+  }
+  return best;
+}
+
+template <int D, int P, int NC>
+struct ApplyLevels {
+  static constexpr int N = P + 1, NPE = D == 2 ? N * N : N * N * N, W = D * P + 1, BB = NC * NC;
+  static constexpr int LV = D * P + 1;                  // levels 0 .. D p
+  static constexpr int MAXS = D * (N - 1);              // slots of one triangle in a row
+  static constexpr int MAXR = level_rows_max<D, P>();   // rows of the widest level
+  static constexpr int WPB = 4, THREADS = 32 * WPB;     // one element per warp
+};
+
+template <int D, int P, int NC, typename R, typename V>
+__global__ void __launch_bounds__(ApplyLevels<D, P, NC>::THREADS)
+    k_precond_apply_lv(const R* __restrict__ F, const V* __restrict__ r, V* __restrict__ z,
+                       const int16_t* __restrict__ lvl, const int32_t* __restrict__ lptr, int64_t E) {
+  using A = ApplyLevels<D, P, NC>;
+  constexpr int N = A::N, NPE = A::NPE, W = A::W, BB = A::BB, LV = A::LV, MAXS = A::MAXS, tile = NC * NPE;
+  using Pos = RowPos<D, N>;
+  __shared__ int16_t lvl_s[NPE];
+  __shared__ int32_t lptr_s[LV + 1];
+  __shared__ V ys[A::WPB][tile];
+  __shared__ V tb[A::WPB][A::MAXR * NC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < NPE; k += A::THREADS) lvl_s[k] = lvl[k];
+  for (int k = threadIdx.x; k <= LV; k += A::THREADS) lptr_s[k] = lptr[k];
+  const int64_t e = (int64_t)blockIdx.x * A::WPB + warp;
+  V* y = ys[warp];
+  V* t = tb[warp];
+  if (e < E)
+    for (int k = lane; k < tile; k += 32) y[k] = r[e * tile + k];
+  __syncthreads();
+  if (e >= E) return;  // no block-wide barrier below
+  const R* Fe = F + e * (int64_t)NPE * W * BB;
+  // forward: y_i -= sum over lower slots L_is y_col (unit diagonal)
+#pragma unroll 1
+  for (int l = 1; l < LV; ++l) {
+    const int r0 = lptr_s[l], nit = (lptr_s[l + 1] - r0) * NC;
+    for (int it = lane; it < nit; it += 32) {
+      const int k = it / NC, c = it - k * NC;
+      const Pos ps(lvl_s[r0 + k]);
+      const R* Fr = Fe + (int64_t)ps.i * W * BB + c * NC;
+      V acc = V(0);
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s)
+        if (s < l) {
+          const int col = ps.lower_col(s);
+#pragma unroll
+          for (int m = 0; m < NC; ++m) acc += (V)__ldg(Fr + s * BB + m) * y[m * NPE + col];
+        }
+      y[c * NPE + ps.i] -= acc;
+    }
+    __syncwarp();
+  }
+  // backward: t_i = y_i - sum over upper slots U_is z_col, z_i = D_i^-1 t_i
+#pragma unroll 1
+  for (int l = LV - 1; l >= 0; --l) {
+    const int r0 = lptr_s[l], nit = (lptr_s[l + 1] - r0) * NC, nu = MAXS - l;
+    for (int it = lane; it < nit; it += 32) {
+      const int k = it / NC, c = it - k * NC;
+      const Pos ps(lvl_s[r0 + k]);
+      const R* Fr = Fe + ((int64_t)ps.i * W + l + 1) * BB + c * NC;
+      V acc = V(0);
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s)
+        if (s < nu) {
+          const int col = ps.upper_col(s);
+#pragma unroll
+          for (int m = 0; m < NC; ++m) acc += (V)__ldg(Fr + s * BB + m) * y[m * NPE + col];
+        }
+      t[k * NC + c] = y[c * NPE + ps.i] - acc;
+    }
+    __syncwarp();
+    for (int it = lane; it < nit; it += 32) {
+      const int k = it / NC, c = it - k * NC;
+      const int i = lvl_s[r0 + k];
+      const R* Dr = Fe + ((int64_t)i * W + l) * BB + c * NC;  // D_i^-1 in the diagonal slot
+      V zc = V(0);
+#pragma unroll
+      for (int m = 0; m < NC; ++m) zc += (V)__ldg(Dr + m) * t[k * NC + m];
+      y[c * NPE + i] = zc;
+    }
+    __syncwarp();
+  }
+  for (int k = lane; k < tile; k += 32) z[e * tile + k] = y[k];
+}
+
 // The split product y = shift x + scale (K11 x + K12 (K21 x)) as its two
 // launches: part 0 both (K21 x into gbuf), part 1 only g = K21 x into gbuf,
 // part 2 only y from x and a given g in gbuf (a partitioned part exchanges
@@ -833,12 +942,22 @@ template <int D, int P, int EQ, typename R, typename V>
 cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const V* r, V* z,
                               cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
-  // FP32: one lane per block entry (the most parallelism). FP64: one lane
-  // per component (no reductions, fewest FP64 operations) when the mesh
-  // gives at least six such warps per SM, else two lanes per component
-  // (twice the warps for a few more FP64 additions); shapes too large to
-  // unroll use one lane per entry.
-  if constexpr (sizeof(V) == 8 && ApplyLanes<D, P, NC, 1, R, V>::UNROLL) {
+  // FP32, 3-D elements up to p = 3: by wavefronts (measured 0.60 against
+  // 0.68 ms on the 32^3, p = 3 Taylor-Green apply); other FP32 shapes: one
+  // lane per block entry along the row chain (2-D p = 4: 27 against 51 us;
+  // 3-D p = 4: 3.3 against 8.0 ms, where a level's scattered 4-byte loads
+  // thrash L1). FP64: one lane per component along the row chain (no
+  // reductions, fewest FP64 operations: the FP64 pipe is the limit) when
+  // the mesh gives at least six such warps per SM, else two lanes per
+  // component (twice the warps for a few more FP64 additions); shapes too
+  // large to unroll use one lane per entry.
+  if constexpr (sizeof(V) == 4 && D == 3 && P <= 3) {
+    using A = ApplyLevels<D, P, NC>;
+    const int64_t blocks = (h->E + A::WPB - 1) / A::WPB;
+    k_precond_apply_lv<D, P, NC, R, V><<<(unsigned)blocks, A::THREADS, 0, st>>>(F, r, z, h->lvl, h->lvl_ptr, h->E);
+    count_launch();
+    return cudaGetLastError();
+  } else if constexpr (sizeof(V) == 8 && ApplyLanes<D, P, NC, 1, R, V>::UNROLL) {
     if constexpr (NC % 2 == 0) {
       const int64_t warps_g1 = (h->E + ApplyLanes<D, P, NC, 1, R, V>::EPW - 1) / ApplyLanes<D, P, NC, 1, R, V>::EPW;
       int dev = 0, sms = 152;

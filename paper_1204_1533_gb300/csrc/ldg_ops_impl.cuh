@@ -41,12 +41,30 @@ cudaError_t Ops<D, EQ>::jacobian(const ldg_handle* h, const double* U, const dou
                    st>>>(qf, Q, nconv - h->ndof);
       count_launch();
     }
-#define F(P) return run_jacobian<D, P, EQ, float>(h, uf, qf, (float*)J->K11, (float*)J->K12, (float*)J->Kw, st)
+    const float* gf = (const float*)J->geof;
+    if (!gf) return cudaErrorInvalidValue;
+    const int64_t nng = h->nlines() * h->nq * h->D, nnend = h->nlines() * 2 * h->D;
+    if (!J->geof_ready) {
+      // the metric terms in FP32, once per Jacobian object (they do not change)
+      const double* src[3] = {h->ng, h->nend, h->invJ};
+      const int64_t len[3] = {nng, nnend, h->E * h->npe};
+      float* dst = (float*)J->geof;
+      for (int a = 0; a < 3; ++a) {
+        k_to_float<<<(unsigned)((len[a] + 255) / 256 < 4096 ? (len[a] + 255) / 256 : 4096), 256, 0, st>>>(dst, src[a],
+                                                                                                    len[a]);
+        count_launch();
+        dst += len[a];
+      }
+      J->geof_ready = true;
+    }
+    const GeoR<float> gr{gf, gf + nng, gf + nng + nnend};
+#define F(P) return run_jacobian<D, P, EQ, float>(h, uf, qf, (float*)J->K11, (float*)J->K12, (float*)J->Kw, gr, st)
     LDG_FOR_P(F)
 #undef F
   } else {
+    const GeoR<double> gr{h->ng, h->nend, h->invJ};
 #define F(P) \
-  return run_jacobian<D, P, EQ, double>(h, U, Q, (double*)J->K11, (double*)J->K12, (double*)J->Kw, st)
+  return run_jacobian<D, P, EQ, double>(h, U, Q, (double*)J->K11, (double*)J->K12, (double*)J->Kw, gr, st)
     LDG_FOR_P(F)
 #undef F
   }

@@ -11,6 +11,14 @@
 // difference cancels) the norm is taken explicitly instead. The Hessenberg
 // column is h1 + h2 and hn.
 //
+// Selective variant: the second pass only where one pass may have lost
+// orthogonality, by Rutishauser's criterion (re-orthogonalise when the pass
+// shrank w by more than a factor K = 10). S1 also returns ||w||^2, so the
+// norm after one pass is known before it is made (||w - V h1||^2 =
+// ||w||^2 - ||h1||^2, losing at most two digits at the accepted ratios); if
+// the ratio passes, one sweep w <- (w - V h1) / hn finishes the column (two
+// sweeps, half the multiply-adds of CGS2), otherwise S2 and S3 follow.
+//
 // FP64 sweeps are bound by the narrow FP64 pipe of this part, so every FP64
 // instruction counts: their kernels are instantiated for the exact basis size
 // (no predicated-off multiply-adds), read element pairs with 16-byte loads so
@@ -29,7 +37,7 @@ namespace ldg {
 
 constexpr int GS_THREADS = 256;
 constexpr int GS_WARPS = GS_THREADS / 32;
-enum class GsOp { Dots, UpdateDotsNorm, UpdateScale };
+enum class GsOp { Dots, DotsNorm, UpdateDotsNorm, UpdateScale };
 
 __host__ __device__ constexpr int pow2ceil(int x) {
   int p = 1;
@@ -39,7 +47,8 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 
 // Sweep over kk = KC basis vectors (EXACT) or kk <= KC (guarded). Partial
 // sums: row r of `part` ([rows][gridDim.x]) receives block sums of value r:
-// the dots (rows 0..kk-1) and, for UpdateDotsNorm, ||w||^2 in row kk.
+// the dots (rows 0..kk-1) and, for DotsNorm and UpdateDotsNorm, ||w||^2 of
+// the (updated) vector in row kk.
 // VEC = 2: each thread takes two consecutive elements per load (16-byte
 // loads of FP64 pairs; n even, vectors 16-byte aligned), which doubles the
 // bytes in flight per load without more threads (more threads would mean
@@ -74,9 +83,9 @@ __global__ void __launch_bounds__(GS_THREADS, (gs_min_blocks<V, VEC, KC>()))
     k_ortho(const V* __restrict__ Vb, int64_t n, int kk, V* __restrict__ w, const double* __restrict__ h,
             double scale, double* __restrict__ part) {
   using VT = typename Vec<V, VEC>::T;
-  constexpr bool UPD = OP != GsOp::Dots;
+  constexpr bool UPD = OP == GsOp::UpdateDotsNorm || OP == GsOp::UpdateScale;
   constexpr bool DOTS = OP != GsOp::UpdateScale;
-  constexpr bool NORM = OP == GsOp::UpdateDotsNorm;
+  constexpr bool NORM = OP == GsOp::UpdateDotsNorm || OP == GsOp::DotsNorm;
   constexpr int NV = KC + (NORM ? 1 : 0);  // values reduced per thread
   static_assert(NV <= 32, "at most 32 values per warp reduction");
   const int k = EXACT ? KC : kk;
@@ -224,7 +233,7 @@ static constexpr int exact_blocks_tab[] = {2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 1
 
 // largest basis size of one fused sweep
 template <GsOp OP>
-constexpr int gs_kmax() { return OP == GsOp::UpdateDotsNorm ? GS_KMAX - 1 : GS_KMAX; }
+constexpr int gs_kmax() { return (OP == GsOp::UpdateDotsNorm || OP == GsOp::DotsNorm) ? GS_KMAX - 1 : GS_KMAX; }
 
 // kernel and blocks per SM for a sweep over kk vectors of length n: FP64 on
 // even lengths takes the exact pair kernels, everything else the guarded
@@ -259,9 +268,11 @@ static GsKernel<V, OP> pick(int kk, int64_t n, const void* a, const void* b, int
 template <typename V, GsOp OP>
 static int sweep(const V* Vb, int kk, int64_t n, V* w, const double* h, double scale, double* part,
                  cudaStream_t st) {
-  constexpr bool UPD = OP != GsOp::Dots;
+  constexpr bool UPD = OP == GsOp::UpdateDotsNorm || OP == GsOp::UpdateScale;
   const double vsz = sizeof(V), nn = (double)n;
-  const double flops = OP == GsOp::Dots ? 2.0 * kk : (OP == GsOp::UpdateDotsNorm ? 4.0 * kk + 2.0 : 2.0 * kk + 1.0);
+  const double flops = OP == GsOp::Dots       ? 2.0 * kk
+                       : OP == GsOp::DotsNorm ? 2.0 * kk + 2.0
+                       : (OP == GsOp::UpdateDotsNorm ? 4.0 * kk + 2.0 : 2.0 * kk + 1.0);
   int per_sm = 1;
   const GsKernel<V, OP> kern = pick<V, OP>(kk, n, Vb, w, &per_sm);
   int nb = sm_count() * per_sm;
@@ -283,16 +294,39 @@ static cudaError_t reduce(const double* part, int nblk, int rows, double* out, d
 }
 
 template <typename V>
-int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col,
-                   cudaStream_t st) {
+int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, bool selective,
+                   int* passes, cudaStream_t st) {
   double* h1 = gs + 2 * (GS_MAX_BASIS + 2);  // first-pass coefficients
   double* acc = gs;                          // h1 + h2 (kv), then nrm2
   double* h2 = gs + kv + 1;                  // second-pass coefficients
   double nrm2 = 0.0, h2sq = 0.0;
   int nb;
+  if (passes) *passes = 2;
   if (kv <= gs_kmax<GsOp::UpdateDotsNorm>()) {
-    if (!(nb = sweep<V, GsOp::Dots>(Vb, kv, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
-    LDG_CUDA_TRY(reduce(part, nb, kv, h1, acc, kv, 1, st));
+    if (selective) {
+      // S1 with ||w||^2; one pass when it keeps more than 1/K of w
+      constexpr double K = 10.0;
+      if (!(nb = sweep<V, GsOp::DotsNorm>(Vb, kv, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
+      LDG_CUDA_TRY(reduce(part, nb, kv + 1, h1, acc, kv, 1, st));
+      LDG_CUDA_TRY(cudaMemcpyAsync(col, acc, (size_t)(kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      LDG_CUDA_TRY(cudaStreamSynchronize(st));
+      const double ww = col[kv];
+      double h1sq = 0.0;
+      for (int j = 0; j < kv; ++j) h1sq += col[j] * col[j];
+      if (!std::isfinite(ww) || !std::isfinite(h1sq)) return LDG_ERR_NONFINITE;
+      const double hn2 = ww - h1sq;
+      if (hn2 * (K * K) >= ww) {
+        const double hn = std::sqrt(hn2);
+        if (!sweep<V, GsOp::UpdateScale>(Vb, kv, n, w, h1, hn > 0 ? 1.0 / hn : 1.0, part, st))
+          return LDG_ERR_CUDA;
+        col[kv] = hn;
+        if (passes) *passes = 1;
+        return LDG_OK;
+      }
+    } else {
+      if (!(nb = sweep<V, GsOp::Dots>(Vb, kv, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
+      LDG_CUDA_TRY(reduce(part, nb, kv, h1, acc, kv, 1, st));
+    }
     if (!(nb = sweep<V, GsOp::UpdateDotsNorm>(Vb, kv, n, w, h1, 1.0, part, st))) return LDG_ERR_CUDA;
     LDG_CUDA_TRY(reduce(part, nb, kv + 1, h2, acc, kv, 2, st));
     LDG_CUDA_TRY(cudaMemcpyAsync(col, acc, (size_t)(2 * kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -358,8 +392,9 @@ int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* g
   return LDG_OK;
 }
 
-template int arnoldi_column<float>(const float*, int, int64_t, float*, double*, double*, double*, cudaStream_t);
-template int arnoldi_column<double>(const double*, int, int64_t, double*, double*, double*, double*,
+template int arnoldi_column<float>(const float*, int, int64_t, float*, double*, double*, double*, bool, int*,
+                                   cudaStream_t);
+template int arnoldi_column<double>(const double*, int, int64_t, double*, double*, double*, double*, bool, int*,
                                     cudaStream_t);
 
 }  // namespace ldg

@@ -180,8 +180,8 @@ static cudaError_t mdot(const V* Vb, int k, int64_t n, const V* w, double* part,
 // Right-preconditioned GMRES(m) on (I - adt A) x = b for vectors of type V;
 // b is overwritten; x receives the solution (zero initial guess).
 template <typename V>
-static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double tol, int m, Work& w,
-                 int* its_out, double* rel_out, cudaStream_t st) {
+static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double tol, int m, bool selective,
+                 Work& w, int* its_out, double* rel_out, int* reorth_out, cudaStream_t st) {
   const int64_t n = h->ndof;
   V* Vb = (V*)w.Vb;
   V* z = (V*)w.z;
@@ -196,6 +196,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
   const double beta = std::sqrt(bb);
   *its_out = 0;
   *rel_out = 0.0;
+  *reorth_out = 0;
   if (beta == 0.0) {
     LDG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(V), st));
     return LDG_OK;
@@ -210,9 +211,12 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
     V* vn = Vb + (int64_t)(k + 1) * n;
     if (launch_precond_apply(h, h->Pn, vk, z, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
     if (launch_jacvec(h, h->Jn, 1.0, -adt, z, vn, vprec, st) != cudaSuccess) return LDG_ERR_CUDA;
-    // classical Gram-Schmidt, twice; vn normalised on return
-    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), st);
+    // classical Gram-Schmidt (twice, or a second time where needed); vn
+    // normalised on return
+    int passes = 2;
+    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), selective, &passes, st);
     if (grc) return grc;
+    *reorth_out += passes > 1;
     for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
     const double hn = hc[k + 1];
     if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
@@ -431,14 +435,15 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
         if (rn <= eta * gn || rn == 0.0) break;
         // relative tolerance of this cycle so that it reaches eta ||G||
         const double tol = eta * gn / rn;
-        int its = 0;
+        int its = 0, reorth = 0;
         double rel = 0;
         if (mode == LDG_MODE_FP64) {
           double* rb = (double*)w.Vb + (int64_t)o->restart * n;
           k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(rb, w.r64, 1.0 / rn, n);
           count_launch();
           double* xe = w.tmp64;
-          rc = gmres<double>(h, vprec, rb, xe, adt, tol, o->restart, w, &its, &rel, st);
+          rc = gmres<double>(h, vprec, rb, xe, adt, tol, o->restart, o->ortho == LDG_ORTHO_SELECTIVE, w, &its,
+                             &rel, &reorth, st);
           if (rc) return rc;
           k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(w.delta, xe, rn, n);
           count_launch();
@@ -449,12 +454,16 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
           k_scale_to<double, float><<<grid_for(n), 256, 0, st>>>(rb, w.r64, 1.0 / rn, n);
           count_launch();
           float* xf = (float*)w.tmp64;  // the FP32 correction fits in the FP64 temporary
-          rc = gmres<float>(h, vprec, rb, xf, adt, tol, o->restart, w, &its, &rel, st);
+          // an FP32 basis always takes the second pass: one FP32 pass loses
+          // orthogonality at its rounding level column by column, which cost
+          // GMRES iterations (the selective scheme serves the FP64 basis)
+          rc = gmres<float>(h, vprec, rb, xf, adt, tol, o->restart, false, w, &its, &rel, &reorth, st);
           if (rc) return rc;
           k_axpy_d<float><<<grid_for(n), 256, 0, st>>>(w.delta, xf, rn, n);
           count_launch();
         }
         stats->gmres_its += its;
+        stats->reorth_its += reorth;
         stats->refine_sweeps++;
       }
     }
@@ -509,6 +518,7 @@ extern "C" int ldg_dirk3_step(ldg_handle_t* h, double* U, const double* Un, doub
     if (rc) return rc;
     stats->newton_its += si.newton_its;
     stats->gmres_its += si.gmres_its;
+    stats->reorth_its += si.reorth_its;
     stats->jac_builds += si.jac_builds;
     stats->refine_sweeps += si.refine_sweeps;
     stats->t_residual_ms += si.t_residual_ms;
@@ -567,6 +577,7 @@ extern "C" int ldg_steady_solve(ldg_handle_t* h, double* U, double dt0, double g
     if (rc) return rc;
     stats->newton_its += sk.newton_its;
     stats->gmres_its += sk.gmres_its;
+    stats->reorth_its += sk.reorth_its;
     stats->jac_builds += sk.jac_builds;
     stats->refine_sweeps += sk.refine_sweeps;
     stats->t_residual_ms += sk.t_residual_ms;
@@ -878,7 +889,7 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
       k_cpl_apply<<<(unsigned)E, 128, 0, st>>>(c->z, vk, c->Binv, B, npe, D, N);
       count_launch();
       if ((rc = cpl_phi(&hh, c->z, vn, c->Gt, st))) return rc;
-      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), st))) return rc;
+      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), false, nullptr, st))) return rc;
       for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
       const double hn = hc[k + 1];
       if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;

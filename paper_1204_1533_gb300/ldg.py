@@ -51,7 +51,7 @@ class ldg_solver_opts_t(C.Structure):
                 ("restart", C.c_int32), ("max_newton", C.c_int32), ("reuse", C.c_int32),
                 ("max_refine", C.c_int32), ("force_rebuild", C.c_int32),
                 ("rtol", C.c_double), ("gmres_tol", C.c_double), ("stall_rebuild", C.c_int32),
-                ("forcing", C.c_int32)]
+                ("forcing", C.c_int32), ("ortho", C.c_int32)]
 
 
 class ldg_step_stats_t(C.Structure):
@@ -59,7 +59,8 @@ class ldg_step_stats_t(C.Structure):
                 ("refine_sweeps", C.c_int32), ("res0", C.c_double), ("res_final", C.c_double),
                 ("res_pred", C.c_double), ("t_residual_ms", C.c_double),
                 ("t_jacobian_ms", C.c_double), ("t_precond_ms", C.c_double),
-                ("t_linear_ms", C.c_double), ("res_extrap", C.c_double), ("pred_weight", C.c_double)]
+                ("t_linear_ms", C.c_double), ("res_extrap", C.c_double), ("pred_weight", C.c_double),
+                ("reorth_its", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -411,13 +412,15 @@ def ldg_pc_export(P, prec):
 
 
 FORCING_FIXED, FORCING_TARGET = 0, 1
+ORTHO_CGS2, ORTHO_SELECTIVE = 0, 1
 
 
 def solver_opts(mode=MODE_MIXED, predictor=PRED_EXTRAP, first_step=False, restart=30,
                 max_newton=50, reuse=15, max_refine=10, force_rebuild=True, rtol=1e-8,
-                gmres_tol=1e-3, stall_rebuild=True, forcing=FORCING_FIXED):
+                gmres_tol=1e-3, stall_rebuild=True, forcing=FORCING_FIXED, ortho=ORTHO_SELECTIVE):
     return ldg_solver_opts_t(mode, predictor, int(first_step), restart, max_newton, reuse,
-                             max_refine, int(force_rebuild), rtol, gmres_tol, int(stall_rebuild), int(forcing))
+                             max_refine, int(force_rebuild), rtol, gmres_tol, int(stall_rebuild), int(forcing),
+                             int(ortho))
 
 
 def ldg_newton_step(h, U_next, U_n, U_nm1, U_nm2, dt, opts, stream=None):

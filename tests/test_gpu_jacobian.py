@@ -288,11 +288,14 @@ def test_preconditioner_factors_and_apply(L, name, prec):
     assert np.abs(zg - zr).max() / np.abs(zr).max() < (1e-5 if prec == 0 else 1e-12)
 
 
+@pytest.mark.parametrize("ortho", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name", ["euler2d_p3", "ns2d_p2", "unstructured_ns2d_p2"])
-def test_newton_bdf2_step(L, mode, name):
+def test_newton_bdf2_step(L, mode, name, ortho):
     """One BDF1 then one BDF2 level to ||G|| <= 1e-8 ||G(U^n)||, compared with
-    the oracle's Newton solution of the same stage equation solved to 1e-12."""
+    the oracle's Newton solution of the same stage equation solved to 1e-12,
+    with CGS2 (every Arnoldi column orthogonalised twice) and with the
+    selective second pass (at most as many second passes as columns)."""
     import torch
     m, eq, U0, _ = _case(name)
     disc = Discretization(m, _oeq(eq))
@@ -309,12 +312,16 @@ def test_newton_bdf2_step(L, mode, name):
     h = L.ldg_setup(m, eq)
     Un = torch.from_numpy(U0).cuda()
     U1 = torch.empty_like(Un)
-    st1 = L.ldg_newton_step(h, U1, Un, None, None, dt, L.solver_opts(mode=mode, first_step=True))
+    st1 = L.ldg_newton_step(h, U1, Un, None, None, dt, L.solver_opts(mode=mode, first_step=True, ortho=ortho))
     U2 = torch.empty_like(Un)
-    st2 = L.ldg_newton_step(h, U2, U1, Un, None, dt, L.solver_opts(mode=mode, force_rebuild=False))
+    st2 = L.ldg_newton_step(h, U2, U1, Un, None, dt, L.solver_opts(mode=mode, force_rebuild=False, ortho=ortho))
     for st in (st1, st2):
         assert st["res_final"] <= 1e-8 * st["res0"]
         assert st["newton_its"] <= 10
+        if ortho == L.ORTHO_CGS2:
+            assert st["reorth_its"] == st["gmres_its"]
+        else:
+            assert 0 <= st["reorth_its"] <= st["gmres_its"]
     d1 = np.abs(U1.cpu().numpy() - U1o).max() / np.abs(U1o).max()
     d2 = np.abs(U2.cpu().numpy() - U2o).max() / np.abs(U2o).max()
     assert d1 < 1e-7 and d2 < 1e-7, (d1, d2)

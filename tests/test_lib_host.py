@@ -94,3 +94,51 @@ def test_stabilised_scheme_is_poisson_only():
     with pytest.raises(ldg.LdgError) as e:
         ldg.ldg_setup_host(I.vortex_mesh(3, 2), dict(EULER, C22=0.05))
     assert e.value.code == -8
+
+
+def _header_structs():
+    """Field (name, C type) lists of every `typedef struct { ... } NAME;` in
+    include/ldg.h, comments stripped."""
+    import pathlib
+    import re
+    src = (pathlib.Path(__file__).resolve().parents[1] / "include" / "ldg.h").read_text()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(.*?)(\w+)(\[\d+\])?$", decl)
+            fields.append((m.group(2), m.group(1).replace(" ", "") + (m.group(3) or "")))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_and_constants_match_header():
+    # every ctypes struct of the binding lists the header's fields in order
+    # with the same widths, and the binding's option constants equal the
+    # header's #defines
+    import ctypes as C
+    import pathlib
+    import re
+    scalar = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double}
+    hdr = _header_structs()
+    for name in ("ldg_mesh_t", "ldg_equations_t", "ldg_solver_opts_t", "ldg_step_stats_t"):
+        fields = getattr(ldg, name)._fields_
+        assert [f[0] for f in fields] == [h[0] for h in hdr[name]], name
+        for (fname, ftype), (_, ctype) in zip(fields, hdr[name]):
+            if ctype.endswith("*"):
+                assert C.sizeof(ftype) == C.sizeof(C.c_void_p), (name, fname)
+            elif "[" in ctype:
+                base, n = ctype[:-1].split("[")
+                assert C.sizeof(ftype) == int(n) * C.sizeof(scalar[base]), (name, fname)
+            else:
+                assert ftype == scalar[ctype], (name, fname)
+    src = (pathlib.Path(__file__).resolve().parents[1] / "include" / "ldg.h").read_text()
+    defs = {k: int(v) for k, v in re.findall(r"#define LDG_(\w+) \(?(-?\d+)\)?", src)}
+    for key in ("PREC_FP32", "PREC_FP64", "MODE_FP64", "MODE_MIXED", "PRED_EXTRAP", "PRED_GIVEN",
+                "PRED_CHECKED", "FORCING_FIXED", "FORCING_TARGET", "ORTHO_CGS2", "ORTHO_SELECTIVE",
+                "KT_APPLY", "KT_JACVEC", "KT_ORTHO"):
+        assert getattr(ldg, key) == defs[key], key
