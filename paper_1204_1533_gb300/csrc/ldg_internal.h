@@ -85,15 +85,18 @@ struct Geo {
 // [GS_PART_LEN], gs [GS_SCRATCH_LEN] doubles. Host col [2 kv + 2]: on
 // return col[0..kv) = Hessenberg entries, col[kv] = the norm before
 // normalisation (0: w lies in the span); *passes (if not null) = the
-// Gram-Schmidt passes made (1 or 2). Synchronises on st.
+// Gram-Schmidt passes made (1 or 2). pin: null, or pinned host memory of
+// GS_PIN_LEN doubles with ev an event, for a read-back that lets the last
+// update sweep run while the host waits. Synchronises on st (on ev).
 constexpr int GS_KMAX = 32;        // basis vectors per fused sweep
 constexpr int GS_MAX_BASIS = 66;   // largest basis (restart 64 + 2)
 constexpr int GS_MAX_BLOCKS = 320;
 constexpr size_t GS_PART_LEN = (size_t)(GS_KMAX + 1) * GS_MAX_BLOCKS;
-constexpr size_t GS_SCRATCH_LEN = 4 * (GS_MAX_BASIS + 2);
+constexpr size_t GS_SCRATCH_LEN = 4 * (GS_MAX_BASIS + 2) + 4;
+constexpr size_t GS_PIN_LEN = GS_MAX_BASIS + 4;  // host read-back of one column
 template <typename V>
 int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, bool selective,
-                   int* passes, cudaStream_t st);
+                   int* passes, double* pin, cudaEvent_t ev, cudaStream_t st);
 
 cudaError_t launch_gradient(const struct ::ldg_handle* h, const double* U, double* Q,
                             cudaStream_t st);
@@ -144,6 +147,8 @@ struct ldg_handle {
   double* red = nullptr;     // reduction scratch (doubles)
   struct ldg_cpl* cpl = nullptr;  // coupled (U, Q) solver state of the stabilised scheme
   int64_t red_len = 0;
+  double* gs_pin = nullptr;    // pinned host read-back of GMRES columns [GS_PIN_LEN]
+  cudaEvent_t gs_ev = nullptr; // marks that read-back
   ldg::Geo geo() const {
     ldg::Geo g;
     g.nbr = nbr;

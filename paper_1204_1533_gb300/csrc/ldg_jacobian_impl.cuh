@@ -172,17 +172,20 @@ __device__ __forceinline__ void end_flux_derivative(const R* uin, const R* uo, c
   if (nb >= 0) {
     inviscid_numflux<EQ, D, T, R>(ux, ui, nv, pp, F);
     if constexpr (VISC) {
-      T qq[NCD], fv[NC];
+      // the viscous flux takes the trace of one side only: its derivative
+      // with respect to the other side is zero and is not evaluated
       const bool from_out = swv == 1;
+      if (from_out == (SIDE == 1)) {
+        T qq[NCD], fv[NC];
 #pragma unroll
-      for (int cb = 0; cb < NCD; ++cb) qq[cb] = dconst<R, NC>(from_out ? qo[cb] : qin[cb]);
-      if (from_out)
-        viscous_flux_n<EQ, D, T, R>(ux, qq, nv, pp, fv);
-      else
-        viscous_flux_n<EQ, D, T, R>(ui, qq, nv, pp, fv);
+        for (int cb = 0; cb < NCD; ++cb) qq[cb] = dconst<R, NC>(from_out ? qo[cb] : qin[cb]);
+        viscous_flux_n<EQ, D, T, R>(SIDE == 1 ? ux : ui, qq, nv, pp, fv);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c];
+      }
       const R pen = pp.C11;  // per unit reference length
 #pragma unroll
-      for (int c = 0; c < NC; ++c) F[c] = F[c] + fv[c] + pen * (ui[c] - ux[c]);
+      for (int c = 0; c < NC; ++c) F[c] = F[c] + pen * (ui[c] - ux[c]);
     }
   } else if (neu || SIDE == 1) {
     // Neumann: the prescribed flux does not depend on the state; walls and

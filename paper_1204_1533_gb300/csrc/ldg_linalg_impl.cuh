@@ -547,10 +547,10 @@ __global__ void __launch_bounds__(256)
 // the G lanes of component c sum their parts, and lane (c, 0) stores the
 // result in the warp's y slice (shared memory). This row-chain form serves
 // the FP64 apply, bound by the FP64 pipe (G = 1 leaves no reduction at all;
-// G = 2 doubles the warps of a small mesh; G = n_c takes element shapes too
-// large to unroll), and the FP32 apply of 2-D and p = 4 elements with
-// G = n_c (the most lanes per element); 3-D FP32 elements up to p = 3 run by
-// wavefronts (k_precond_apply_lv below).
+// G = 2 doubles the warps of a small mesh), the FP32 apply of 2-D elements
+// with G = n_c (the most lanes per element) and of 3-D p = 4 elements with
+// G = 1; 3-D FP32 elements up to p = 3 run by wavefronts
+// (k_precond_apply_lv below).
 //
 // Row i = ix + N iy + N^2 iz couples to the nodes of its D lines; its
 // pattern slots in ascending column order are: lower z, lower y, lower x,
@@ -942,21 +942,30 @@ template <int D, int P, int EQ, typename R, typename V>
 cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const V* r, V* z,
                               cudaStream_t st) {
   constexpr int NC = NComp<EQ, D>::value;
-  // FP32, 3-D elements up to p = 3: by wavefronts (measured 0.60 against
-  // 0.68 ms on the 32^3, p = 3 Taylor-Green apply); other FP32 shapes: one
-  // lane per block entry along the row chain (2-D p = 4: 27 against 51 us;
-  // 3-D p = 4: 3.3 against 8.0 ms, where a level's scattered 4-byte loads
-  // thrash L1). FP64: one lane per component along the row chain (no
-  // reductions, fewest FP64 operations: the FP64 pipe is the limit) when
-  // the mesh gives at least six such warps per SM, else two lanes per
-  // component (twice the warps for a few more FP64 additions); shapes too
-  // large to unroll use one lane per entry.
+  // FP32, 3-D elements up to p = 3: by wavefronts (measured 0.59 against
+  // 0.68 ms on the 32^3, p = 3 Taylor-Green apply; 0.94 ms for one lane per
+  // component). FP32 3-D p = 4: one lane per component along the row chain,
+  // rolled (six elements per warp, no group sums; 0.41 against 0.52 ms for
+  // one lane per entry on a 32 x 16 x 16 channel; by wavefronts the full
+  // channel took 8.0 against 3.3 ms, a level's scattered 4-byte loads of 13
+  // slots thrashing L1). FP32 2-D: one
+  // lane per block entry (27 against 32 us for one lane per component and
+  // 51 us by wavefronts, 64^2 p = 4). FP64: one lane per component along
+  // the row chain (no reductions, fewest FP64 operations: the FP64 pipe is
+  // the limit) when the mesh gives at least six such warps per SM, else two
+  // lanes per component (twice the warps for a few more FP64 additions);
+  // element shapes too large to unroll (3-D) run the same lanes rolled
+  // (1.55 against 3.55 ms for one lane per entry on the 32^3, p = 3
+  // Taylor-Green mesh; 1.49 against 2.06 ms on the 32 x 16 x 16, p = 4
+  // channel).
   if constexpr (sizeof(V) == 4 && D == 3 && P <= 3) {
     using A = ApplyLevels<D, P, NC>;
     const int64_t blocks = (h->E + A::WPB - 1) / A::WPB;
     k_precond_apply_lv<D, P, NC, R, V><<<(unsigned)blocks, A::THREADS, 0, st>>>(F, r, z, h->lvl, h->lvl_ptr, h->E);
     count_launch();
     return cudaGetLastError();
+  } else if constexpr (sizeof(V) == 4 && D == 3) {
+    return launch_apply_lanes<D, P, NC, 1, R, V>(h, F, r, z, st);
   } else if constexpr (sizeof(V) == 8 && ApplyLanes<D, P, NC, 1, R, V>::UNROLL) {
     if constexpr (NC % 2 == 0) {
       const int64_t warps_g1 = (h->E + ApplyLanes<D, P, NC, 1, R, V>::EPW - 1) / ApplyLanes<D, P, NC, 1, R, V>::EPW;
@@ -964,6 +973,8 @@ cudaError_t run_precond_apply(const ldg_handle* h, const R* F, const V* r, V* z,
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (warps_g1 < 6 * (int64_t)sms) return launch_apply_lanes<D, P, NC, 2, R, V>(h, F, r, z, st);
     }
+    return launch_apply_lanes<D, P, NC, 1, R, V>(h, F, r, z, st);
+  } else if constexpr (sizeof(V) == 8) {
     return launch_apply_lanes<D, P, NC, 1, R, V>(h, F, r, z, st);
   } else {
     return launch_apply_lanes<D, P, NC, NC, R, V>(h, F, r, z, st);

@@ -81,8 +81,18 @@ constexpr int gs_min_blocks() {
 template <typename V, GsOp OP, int KC, bool EXACT, int VEC>
 __global__ void __launch_bounds__(GS_THREADS, (gs_min_blocks<V, VEC, KC>()))
     k_ortho(const V* __restrict__ Vb, int64_t n, int kk, V* __restrict__ w, const double* __restrict__ h,
-            double scale, double* __restrict__ part) {
+            double scale, const double* __restrict__ dsc, double* __restrict__ part) {
   using VT = typename Vec<V, VEC>::T;
+  // UpdateScale with a device scale (dsc, written by k_gs_reduce_scale):
+  // 0 means the column needs another pass and this sweep does nothing
+  V sc = (V)scale;
+  if constexpr (OP == GsOp::UpdateScale) {
+    if (dsc) {
+      const double sd = dsc[0];
+      if (sd == 0.0) return;
+      sc = (V)sd;
+    }
+  }
   constexpr bool UPD = OP == GsOp::UpdateDotsNorm || OP == GsOp::UpdateScale;
   constexpr bool DOTS = OP != GsOp::UpdateScale;
   constexpr bool NORM = OP == GsOp::UpdateDotsNorm || OP == GsOp::DotsNorm;
@@ -96,7 +106,6 @@ __global__ void __launch_bounds__(GS_THREADS, (gs_min_blocks<V, VEC, KC>()))
   V acc[NV > 0 ? NV : 1];
 #pragma unroll
   for (int j = 0; j < NV; ++j) acc[j] = V(0);
-  const V sc = (V)scale;
   const int64_t nv = n / VEC;
   const VT* Vv = reinterpret_cast<const VT*>(Vb);
   VT* wv = reinterpret_cast<VT*>(w);
@@ -193,6 +202,44 @@ __global__ void k_gs_reduce(const double* __restrict__ part, int nblk, double* _
   }
 }
 
+// k_gs_reduce for rows <= 64 in one block, then the column's norm after the
+// pass from its rows (V orthonormal: ||w - V h||^2 = ||w||^2 - ||h||^2, with
+// h = rows 0..kv-1 and ||w||^2 = row kv): accepted when the difference keeps
+// at least 1/thr of ||w||^2; sc[0] = 1/hn (1 when hn = 0) or 0 when not
+// accepted, sc[1] = hn.
+__global__ void __launch_bounds__(256) k_gs_reduce_scale(const double* __restrict__ part, int nblk, int rows,
+                                                         double* __restrict__ out, double* __restrict__ acc,
+                                                         int nacc, int mode, int kv, double thr,
+                                                         double* __restrict__ sc) {
+  __shared__ double val[64];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int r = wp; r < rows; r += 8) {
+    double s = 0.0;
+    for (int i = lane; i < nblk; i += 32) s += part[(int64_t)r * nblk + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      val[r] = s;
+      if (out) out[r] = s;
+      if (acc) {
+        if (r < nacc && mode == 2)
+          acc[r] += s;
+        else if (mode != 0)
+          acc[r] = s;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ssq = 0.0;
+    for (int j = 0; j < kv; ++j) ssq += val[j] * val[j];
+    const double ww = val[kv], hn2 = ww - ssq;
+    const bool ok = isfinite(ww) && isfinite(ssq) && hn2 >= 0.0 && hn2 * thr >= ww;
+    const double hn = ok ? sqrt(hn2) : 0.0;
+    sc[0] = ok ? (hn > 0.0 ? 1.0 / hn : 1.0) : 0.0;
+    sc[1] = hn;
+  }
+}
+
 template <typename V>
 __global__ void k_gs_scale(V* __restrict__ w, double s, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -221,7 +268,7 @@ static int gs_blocks() {
 
 // ---- dispatch tables -------------------------------------------------------
 template <typename V, GsOp OP>
-using GsKernel = void (*)(const V*, int64_t, int, V*, const double*, double, double*);
+using GsKernel = void (*)(const V*, int64_t, int, V*, const double*, double, const double*, double*);
 
 template <typename V, GsOp OP, int... K>
 static GsKernel<V, OP> exact_kernel(int kk, std::integer_sequence<int, K...>) {
@@ -267,7 +314,7 @@ static GsKernel<V, OP> pick(int kk, int64_t n, const void* a, const void* b, int
 // returns the number of blocks (0 on a launch error).
 template <typename V, GsOp OP>
 static int sweep(const V* Vb, int kk, int64_t n, V* w, const double* h, double scale, double* part,
-                 cudaStream_t st) {
+                 cudaStream_t st, const double* dsc = nullptr) {
   constexpr bool UPD = OP == GsOp::UpdateDotsNorm || OP == GsOp::UpdateScale;
   const double vsz = sizeof(V), nn = (double)n;
   const double flops = OP == GsOp::Dots       ? 2.0 * kk
@@ -280,7 +327,7 @@ static int sweep(const V* Vb, int kk, int64_t n, V* w, const double* h, double s
   {
     TimedScope tl(KT_ORTHO, sizeof(V) == 4 ? LDG_PREC_FP32 : LDG_PREC_FP64, st,
                   nn * vsz * (kk + 1 + (UPD ? 1 : 0)), nn * flops);
-    kern<<<nb, GS_THREADS, 0, st>>>(Vb, n, kk, w, h, scale, part);
+    kern<<<nb, GS_THREADS, 0, st>>>(Vb, n, kk, w, h, scale, dsc, part);
   }
   count_launch();
   return cudaGetLastError() == cudaSuccess ? nb : 0;
@@ -292,34 +339,58 @@ static cudaError_t reduce(const double* part, int nblk, int rows, double* out, d
   count_launch();
   return cudaGetLastError();
 }
+static cudaError_t reduce_scale(const double* part, int nblk, int rows, double* out, double* acc, int nacc, int mode,
+                                int kv, double thr, double* sc, cudaStream_t st) {
+  k_gs_reduce_scale<<<1, 256, 0, st>>>(part, nblk, rows, out, acc, nacc, mode, kv, thr, sc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// the column read-back: acc[0..kv] and sc[0..1] to host (pinned when pin is
+// given: the copies are queued and the event marks them, so the GPU goes on
+// with the update sweep while the host waits), into col[0..kv] and
+// col[kv + 1], col[kv + 2]
+static cudaError_t read_column(const double* acc, const double* sc, int kv, double* col, double* pin,
+                               cudaEvent_t ev, cudaStream_t st) {
+  double* dst = pin ? pin : col;
+  cudaError_t e = cudaMemcpyAsync(dst, acc, (size_t)(kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst + kv + 1, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev, st);
+  return e;
+}
+static cudaError_t wait_column(int kv, double* col, const double* pin, cudaEvent_t ev, cudaStream_t st) {
+  cudaError_t e = ev ? cudaEventSynchronize(ev) : cudaStreamSynchronize(st);
+  if (e == cudaSuccess && pin)
+    for (int j = 0; j < kv + 3; ++j) col[j] = pin[j];
+  return e;
+}
 
 template <typename V>
 int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, bool selective,
-                   int* passes, cudaStream_t st) {
+                   int* passes, double* pin, cudaEvent_t ev, cudaStream_t st) {
   double* h1 = gs + 2 * (GS_MAX_BASIS + 2);  // first-pass coefficients
-  double* acc = gs;                          // h1 + h2 (kv), then nrm2
+  double* acc = gs;                          // h1 + h2 (kv), then the norm row
   double* h2 = gs + kv + 1;                  // second-pass coefficients
-  double nrm2 = 0.0, h2sq = 0.0;
+  double* sc = gs + 4 * (GS_MAX_BASIS + 2);  // device scale of the update sweep, hn
   int nb;
   if (passes) *passes = 2;
   if (kv <= gs_kmax<GsOp::UpdateDotsNorm>()) {
+    // each pass's reduction also forms the norm after the pass and its
+    // scale on the device, so the update + scale sweep is queued before the
+    // host reads the column; it does nothing when the pass is not accepted
     if (selective) {
       // S1 with ||w||^2; one pass when it keeps more than 1/K of w
       constexpr double K = 10.0;
       if (!(nb = sweep<V, GsOp::DotsNorm>(Vb, kv, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
-      LDG_CUDA_TRY(reduce(part, nb, kv + 1, h1, acc, kv, 1, st));
-      LDG_CUDA_TRY(cudaMemcpyAsync(col, acc, (size_t)(kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      LDG_CUDA_TRY(cudaStreamSynchronize(st));
-      const double ww = col[kv];
+      LDG_CUDA_TRY(reduce_scale(part, nb, kv + 1, h1, acc, kv, 1, kv, K * K, sc, st));
+      LDG_CUDA_TRY(read_column(acc, sc, kv, col, pin, ev, st));
+      if (!sweep<V, GsOp::UpdateScale>(Vb, kv, n, w, h1, 1.0, part, st, sc)) return LDG_ERR_CUDA;
+      LDG_CUDA_TRY(wait_column(kv, col, pin, ev, st));
       double h1sq = 0.0;
       for (int j = 0; j < kv; ++j) h1sq += col[j] * col[j];
-      if (!std::isfinite(ww) || !std::isfinite(h1sq)) return LDG_ERR_NONFINITE;
-      const double hn2 = ww - h1sq;
-      if (hn2 * (K * K) >= ww) {
-        const double hn = std::sqrt(hn2);
-        if (!sweep<V, GsOp::UpdateScale>(Vb, kv, n, w, h1, hn > 0 ? 1.0 / hn : 1.0, part, st))
-          return LDG_ERR_CUDA;
-        col[kv] = hn;
+      if (!std::isfinite(col[kv]) || !std::isfinite(h1sq)) return LDG_ERR_NONFINITE;
+      if (col[kv + 1] != 0.0) {
+        col[kv] = col[kv + 2];
         if (passes) *passes = 1;
         return LDG_OK;
       }
@@ -327,52 +398,21 @@ int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* g
       if (!(nb = sweep<V, GsOp::Dots>(Vb, kv, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
       LDG_CUDA_TRY(reduce(part, nb, kv, h1, acc, kv, 1, st));
     }
+    // second pass; the norm after it from its dots (Pythagoras) unless the
+    // pass removed nearly all of w
+    const double guard = sizeof(V) == 8 ? 1e-4 : 1e-2;
     if (!(nb = sweep<V, GsOp::UpdateDotsNorm>(Vb, kv, n, w, h1, 1.0, part, st))) return LDG_ERR_CUDA;
-    LDG_CUDA_TRY(reduce(part, nb, kv + 1, h2, acc, kv, 2, st));
-    LDG_CUDA_TRY(cudaMemcpyAsync(col, acc, (size_t)(2 * kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LDG_CUDA_TRY(cudaStreamSynchronize(st));
-    nrm2 = col[kv];
-    for (int j = 0; j < kv; ++j) h2sq += col[kv + 1 + j] * col[kv + 1 + j];
-  } else {
-    // chunks of GS_KMAX vectors: both passes as dots then update sweeps
-    for (int pass = 0; pass < 2; ++pass) {
-      double* hp = pass ? h2 : h1;
-      for (int j0 = 0; j0 < kv; j0 += GS_KMAX) {
-        const int kk = kv - j0 < GS_KMAX ? kv - j0 : GS_KMAX;
-        if (!(nb = sweep<V, GsOp::Dots>(Vb + (int64_t)j0 * n, kk, n, w, nullptr, 1.0, part, st)))
-          return LDG_ERR_CUDA;
-        LDG_CUDA_TRY(reduce(part, nb, kk, hp + j0, acc + j0, kk, pass ? 2 : 1, st));
-      }
-      for (int j0 = 0; j0 < kv; j0 += GS_KMAX) {
-        const int kk = kv - j0 < GS_KMAX ? kv - j0 : GS_KMAX;
-        if (!sweep<V, GsOp::UpdateScale>(Vb + (int64_t)j0 * n, kk, n, w, hp + j0, 1.0, part, st))
-          return LDG_ERR_CUDA;
-      }
+    LDG_CUDA_TRY(reduce_scale(part, nb, kv + 1, h2, acc, kv, 2, kv, 1.0 / guard, sc, st));
+    LDG_CUDA_TRY(read_column(acc, sc, kv, col, pin, ev, st));
+    if (!sweep<V, GsOp::UpdateScale>(Vb, kv, n, w, h2, 1.0, part, st, sc)) return LDG_ERR_CUDA;
+    LDG_CUDA_TRY(wait_column(kv, col, pin, ev, st));
+    double asq = 0.0;
+    for (int j = 0; j < kv; ++j) asq += col[j] * col[j];
+    if (!std::isfinite(col[kv]) || !std::isfinite(asq)) return LDG_ERR_NONFINITE;
+    if (col[kv + 1] != 0.0) {
+      col[kv] = col[kv + 2];
+      return LDG_OK;
     }
-    if (!(nb = sweep<V, GsOp::Dots>(w, 1, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
-    LDG_CUDA_TRY(reduce(part, nb, 1, nullptr, acc + kv, 0, 1, st));
-    LDG_CUDA_TRY(cudaMemcpyAsync(col, acc, (size_t)(kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LDG_CUDA_TRY(cudaStreamSynchronize(st));
-    const double hn = std::sqrt(col[kv]);
-    if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
-    if (hn > 0) {
-      k_gs_scale<V><<<gs_blocks<V>(), GS_THREADS, 0, st>>>(w, 1.0 / hn, n);
-      count_launch();
-      LDG_CUDA_TRY(cudaGetLastError());
-    }
-    col[kv] = hn;
-    return LDG_OK;
-  }
-  // fused path: the norm after the third pass from the second (Pythagoras),
-  // unless the second pass removed nearly all of w
-  const double guard = sizeof(V) == 8 ? 1e-4 : 1e-2;
-  const double hn2 = nrm2 - h2sq;
-  if (!std::isfinite(nrm2) || !std::isfinite(h2sq)) return LDG_ERR_NONFINITE;
-  double hn;
-  if (hn2 >= guard * nrm2) {
-    hn = std::sqrt(hn2);
-    if (!sweep<V, GsOp::UpdateScale>(Vb, kv, n, w, h2, hn > 0 ? 1.0 / hn : 1.0, part, st)) return LDG_ERR_CUDA;
-  } else {
     // explicit third sweep: w -= V h2 with its norm (its dots are not used)
     double* g3 = gs + 3 * (GS_MAX_BASIS + 2);
     if (!(nb = sweep<V, GsOp::UpdateDotsNorm>(Vb, kv, n, w, h2, 1.0, part, st))) return LDG_ERR_CUDA;
@@ -381,20 +421,46 @@ int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* g
     LDG_CUDA_TRY(cudaMemcpyAsync(&nn2, g3 + kv, sizeof(double), cudaMemcpyDeviceToHost, st));
     LDG_CUDA_TRY(cudaStreamSynchronize(st));
     if (!std::isfinite(nn2)) return LDG_ERR_NONFINITE;
-    hn = std::sqrt(nn2);
+    const double hn = std::sqrt(nn2);
     if (hn > 0) {
       k_gs_scale<V><<<gs_blocks<V>(), GS_THREADS, 0, st>>>(w, 1.0 / hn, n);
       count_launch();
       LDG_CUDA_TRY(cudaGetLastError());
     }
+    col[kv] = hn;
+    return LDG_OK;
+  }
+  // chunks of GS_KMAX vectors: both passes as dots then update sweeps
+  for (int pass = 0; pass < 2; ++pass) {
+    double* hp = pass ? h2 : h1;
+    for (int j0 = 0; j0 < kv; j0 += GS_KMAX) {
+      const int kk = kv - j0 < GS_KMAX ? kv - j0 : GS_KMAX;
+      if (!(nb = sweep<V, GsOp::Dots>(Vb + (int64_t)j0 * n, kk, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
+      LDG_CUDA_TRY(reduce(part, nb, kk, hp + j0, acc + j0, kk, pass ? 2 : 1, st));
+    }
+    for (int j0 = 0; j0 < kv; j0 += GS_KMAX) {
+      const int kk = kv - j0 < GS_KMAX ? kv - j0 : GS_KMAX;
+      if (!sweep<V, GsOp::UpdateScale>(Vb + (int64_t)j0 * n, kk, n, w, hp + j0, 1.0, part, st)) return LDG_ERR_CUDA;
+    }
+  }
+  if (!(nb = sweep<V, GsOp::Dots>(w, 1, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
+  LDG_CUDA_TRY(reduce(part, nb, 1, nullptr, acc + kv, 0, 1, st));
+  LDG_CUDA_TRY(cudaMemcpyAsync(col, acc, (size_t)(kv + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  LDG_CUDA_TRY(cudaStreamSynchronize(st));
+  const double hn = std::sqrt(col[kv]);
+  if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
+  if (hn > 0) {
+    k_gs_scale<V><<<gs_blocks<V>(), GS_THREADS, 0, st>>>(w, 1.0 / hn, n);
+    count_launch();
+    LDG_CUDA_TRY(cudaGetLastError());
   }
   col[kv] = hn;
   return LDG_OK;
 }
 
 template int arnoldi_column<float>(const float*, int, int64_t, float*, double*, double*, double*, bool, int*,
-                                   cudaStream_t);
+                                   double*, cudaEvent_t, cudaStream_t);
 template int arnoldi_column<double>(const double*, int, int64_t, double*, double*, double*, double*, bool, int*,
-                                    cudaStream_t);
+                                    double*, cudaEvent_t, cudaStream_t);
 
 }  // namespace ldg

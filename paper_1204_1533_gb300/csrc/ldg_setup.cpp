@@ -666,6 +666,8 @@ extern "C" int ldg_setup_host(const ldg_mesh_t* mesh, const ldg_equations_t* eq,
 
 extern "C" int ldg_destroy(ldg_handle_t* h) {
   if (!h) return LDG_OK;
+  if (h->gs_pin) cudaFreeHost(h->gs_pin);
+  if (h->gs_ev) cudaEventDestroy(h->gs_ev);
   ldg_jac_destroy(h->Jn);
   ldg_pc_destroy(h->Pn);
   cudaFree(h->ws);

@@ -120,6 +120,8 @@ struct Work {
   double* hcol;                               // [m+2]
   double* hacc;                               // Gram-Schmidt scratch [GS_SCRATCH_LEN]
   double* y;                                  // [m+1]
+  double* pin;                                // pinned host read-back [GS_PIN_LEN]
+  cudaEvent_t ev;                             // marks the read-back
 };
 
 static size_t part_len(int m) {
@@ -134,6 +136,11 @@ static size_t work_bytes(const ldg_handle* h, int m, int vbytes) {
 }
 
 static int get_work(ldg_handle* h, int m, int vbytes, Work& w) {
+  if (!h->gs_pin && cudaHostAlloc((void**)&h->gs_pin, GS_PIN_LEN * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+    return LDG_ERR_CUDA;
+  if (!h->gs_ev && cudaEventCreateWithFlags(&h->gs_ev, cudaEventDisableTiming) != cudaSuccess) return LDG_ERR_CUDA;
+  w.pin = h->gs_pin;
+  w.ev = h->gs_ev;
   const size_t need = work_bytes(h, m, 8);  // sized for FP64 so either mode fits
   if (h->ws_bytes < need) {
     cudaFree(h->ws);
@@ -214,7 +221,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
     // classical Gram-Schmidt (twice, or a second time where needed); vn
     // normalised on return
     int passes = 2;
-    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), selective, &passes, st);
+    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), selective, &passes, w.pin, w.ev, st);
     if (grc) return grc;
     *reorth_out += passes > 1;
     for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
@@ -889,7 +896,8 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
       k_cpl_apply<<<(unsigned)E, 128, 0, st>>>(c->z, vk, c->Binv, B, npe, D, N);
       count_launch();
       if ((rc = cpl_phi(&hh, c->z, vn, c->Gt, st))) return rc;
-      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), false, nullptr, st))) return rc;
+      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), false, nullptr, nullptr, nullptr,
+                                        st))) return rc;
       for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
       const double hn = hc[k + 1];
       if (!std::isfinite(hn)) return LDG_ERR_NONFINITE;
