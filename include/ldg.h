@@ -346,6 +346,9 @@ typedef struct {
                             solve (not in the paper)                          */
   int32_t ortho;         /* LDG_ORTHO_*: Gram-Schmidt of the Arnoldi columns
                             (the paper does not name one)                     */
+  double reorth_factor;  /* LDG_ORTHO_SELECTIVE: a second pass when the first
+                            shrinks the column by more than this factor
+                            (<= 0: 10, Rutishauser's value; 1: always)        */
 } ldg_solver_opts_t;
 
 #define LDG_ORTHO_CGS2 0      /* classical Gram-Schmidt, always twice          */

@@ -78,9 +78,9 @@ struct Geo {
   int64_t E;
 };
 
-// Arnoldi column of GMRES by CGS2, or with selective = true by classical
+// Arnoldi column of GMRES by CGS2 (reorth_k <= 0), or by classical
 // Gram-Schmidt re-orthogonalised only where one pass shrank w by more than
-// a factor 10 (ldg_ortho.cu): orthogonalises w against the kv basis vectors
+// a factor reorth_k (ldg_ortho.cu): orthogonalises w against the kv basis vectors
 // Vb[0..kv) (stride n) and normalises it. Device scratch: part
 // [GS_PART_LEN], gs [GS_SCRATCH_LEN] doubles. Host col [2 kv + 2]: on
 // return col[0..kv) = Hessenberg entries, col[kv] = the norm before
@@ -95,7 +95,7 @@ constexpr size_t GS_PART_LEN = (size_t)(GS_KMAX + 1) * GS_MAX_BLOCKS;
 constexpr size_t GS_SCRATCH_LEN = 4 * (GS_MAX_BASIS + 2) + 4;
 constexpr size_t GS_PIN_LEN = GS_MAX_BASIS + 4;  // host read-back of one column
 template <typename V>
-int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, bool selective,
+int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, double reorth_k,
                    int* passes, double* pin, cudaEvent_t ev, cudaStream_t st);
 
 cudaError_t launch_gradient(const struct ::ldg_handle* h, const double* U, double* Q,

@@ -13,7 +13,7 @@
 //
 // Selective variant: the second pass only where one pass may have lost
 // orthogonality, by Rutishauser's criterion (re-orthogonalise when the pass
-// shrank w by more than a factor K = 10). S1 also returns ||w||^2, so the
+// shrank w by more than a factor K, 10 by default). S1 also returns ||w||^2, so the
 // norm after one pass is known before it is made (||w - V h1||^2 =
 // ||w||^2 - ||h1||^2, losing at most two digits at the accepted ratios); if
 // the ratio passes, one sweep w <- (w - V h1) / hn finishes the column (two
@@ -366,7 +366,7 @@ static cudaError_t wait_column(int kv, double* col, const double* pin, cudaEvent
 }
 
 template <typename V>
-int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, bool selective,
+int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* gs, double* col, double reorth_k,
                    int* passes, double* pin, cudaEvent_t ev, cudaStream_t st) {
   double* h1 = gs + 2 * (GS_MAX_BASIS + 2);  // first-pass coefficients
   double* acc = gs;                          // h1 + h2 (kv), then the norm row
@@ -378,9 +378,9 @@ int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* g
     // each pass's reduction also forms the norm after the pass and its
     // scale on the device, so the update + scale sweep is queued before the
     // host reads the column; it does nothing when the pass is not accepted
-    if (selective) {
+    if (reorth_k > 0.0) {
       // S1 with ||w||^2; one pass when it keeps more than 1/K of w
-      constexpr double K = 10.0;
+      const double K = reorth_k;
       if (!(nb = sweep<V, GsOp::DotsNorm>(Vb, kv, n, w, nullptr, 1.0, part, st))) return LDG_ERR_CUDA;
       LDG_CUDA_TRY(reduce_scale(part, nb, kv + 1, h1, acc, kv, 1, kv, K * K, sc, st));
       LDG_CUDA_TRY(read_column(acc, sc, kv, col, pin, ev, st));
@@ -458,9 +458,9 @@ int arnoldi_column(const V* Vb, int kv, int64_t n, V* w, double* part, double* g
   return LDG_OK;
 }
 
-template int arnoldi_column<float>(const float*, int, int64_t, float*, double*, double*, double*, bool, int*,
+template int arnoldi_column<float>(const float*, int, int64_t, float*, double*, double*, double*, double, int*,
                                    double*, cudaEvent_t, cudaStream_t);
-template int arnoldi_column<double>(const double*, int, int64_t, double*, double*, double*, double*, bool, int*,
+template int arnoldi_column<double>(const double*, int, int64_t, double*, double*, double*, double*, double, int*,
                                     double*, cudaEvent_t, cudaStream_t);
 
 }  // namespace ldg

@@ -187,7 +187,7 @@ static cudaError_t mdot(const V* Vb, int k, int64_t n, const V* w, double* part,
 // Right-preconditioned GMRES(m) on (I - adt A) x = b for vectors of type V;
 // b is overwritten; x receives the solution (zero initial guess).
 template <typename V>
-static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double tol, int m, bool selective,
+static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double tol, int m, double reorth_k,
                  Work& w, int* its_out, double* rel_out, int* reorth_out, cudaStream_t st) {
   const int64_t n = h->ndof;
   V* Vb = (V*)w.Vb;
@@ -221,7 +221,7 @@ static int gmres(ldg_handle* h, int vprec, const V* b, V* x, double adt, double 
     // classical Gram-Schmidt (twice, or a second time where needed); vn
     // normalised on return
     int passes = 2;
-    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), selective, &passes, w.pin, w.ev, st);
+    int grc = arnoldi_column<V>(Vb, k + 1, n, vn, w.part, w.hacc, hc.data(), reorth_k, &passes, w.pin, w.ev, st);
     if (grc) return grc;
     *reorth_out += passes > 1;
     for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
@@ -449,8 +449,9 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
           k_scale_to<double, double><<<grid_for(n), 256, 0, st>>>(rb, w.r64, 1.0 / rn, n);
           count_launch();
           double* xe = w.tmp64;
-          rc = gmres<double>(h, vprec, rb, xe, adt, tol, o->restart, o->ortho == LDG_ORTHO_SELECTIVE, w, &its,
-                             &rel, &reorth, st);
+          const double rk =
+              o->ortho == LDG_ORTHO_SELECTIVE ? (o->reorth_factor > 0.0 ? o->reorth_factor : 10.0) : 0.0;
+          rc = gmres<double>(h, vprec, rb, xe, adt, tol, o->restart, rk, w, &its, &rel, &reorth, st);
           if (rc) return rc;
           k_axpy_d<double><<<grid_for(n), 256, 0, st>>>(w.delta, xe, rn, n);
           count_launch();
@@ -464,7 +465,7 @@ extern "C" int ldg_newton_step(ldg_handle_t* h, double* U, const double* Un, con
           // an FP32 basis always takes the second pass: one FP32 pass loses
           // orthogonality at its rounding level column by column, which cost
           // GMRES iterations (the selective scheme serves the FP64 basis)
-          rc = gmres<float>(h, vprec, rb, xf, adt, tol, o->restart, false, w, &its, &rel, &reorth, st);
+          rc = gmres<float>(h, vprec, rb, xf, adt, tol, o->restart, 0.0, w, &its, &rel, &reorth, st);
           if (rc) return rc;
           k_axpy_d<float><<<grid_for(n), 256, 0, st>>>(w.delta, xf, rn, n);
           count_launch();
@@ -896,7 +897,7 @@ extern "C" int ldg_coupled_solve(ldg_handle_t* h, double* U, double* Q, double r
       k_cpl_apply<<<(unsigned)E, 128, 0, st>>>(c->z, vk, c->Binv, B, npe, D, N);
       count_launch();
       if ((rc = cpl_phi(&hh, c->z, vn, c->Gt, st))) return rc;
-      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), false, nullptr, nullptr, nullptr,
+      if ((rc = arnoldi_column<double>(c->Vb, k + 1, M, vn, c->part, c->hacc, hc.data(), 0.0, nullptr, nullptr, nullptr,
                                         st))) return rc;
       for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hc[j];
       const double hn = hc[k + 1];

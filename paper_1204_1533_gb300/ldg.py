@@ -51,7 +51,7 @@ class ldg_solver_opts_t(C.Structure):
                 ("restart", C.c_int32), ("max_newton", C.c_int32), ("reuse", C.c_int32),
                 ("max_refine", C.c_int32), ("force_rebuild", C.c_int32),
                 ("rtol", C.c_double), ("gmres_tol", C.c_double), ("stall_rebuild", C.c_int32),
-                ("forcing", C.c_int32), ("ortho", C.c_int32)]
+                ("forcing", C.c_int32), ("ortho", C.c_int32), ("reorth_factor", C.c_double)]
 
 
 class ldg_step_stats_t(C.Structure):
@@ -417,10 +417,11 @@ ORTHO_CGS2, ORTHO_SELECTIVE = 0, 1
 
 def solver_opts(mode=MODE_MIXED, predictor=PRED_EXTRAP, first_step=False, restart=30,
                 max_newton=50, reuse=15, max_refine=10, force_rebuild=True, rtol=1e-8,
-                gmres_tol=1e-3, stall_rebuild=True, forcing=FORCING_FIXED, ortho=ORTHO_SELECTIVE):
+                gmres_tol=1e-3, stall_rebuild=True, forcing=FORCING_FIXED, ortho=ORTHO_SELECTIVE,
+                reorth_factor=0.0):
     return ldg_solver_opts_t(mode, predictor, int(first_step), restart, max_newton, reuse,
                              max_refine, int(force_rebuild), rtol, gmres_tol, int(stall_rebuild), int(forcing),
-                             int(ortho))
+                             int(ortho), float(reorth_factor))
 
 
 def ldg_newton_step(h, U_next, U_n, U_nm1, U_nm2, dt, opts, stream=None):

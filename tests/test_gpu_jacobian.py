@@ -288,14 +288,16 @@ def test_preconditioner_factors_and_apply(L, name, prec):
     assert np.abs(zg - zr).max() / np.abs(zr).max() < (1e-5 if prec == 0 else 1e-12)
 
 
-@pytest.mark.parametrize("ortho", [0, 1])
+@pytest.mark.parametrize("ortho", ["cgs2", "selective", "selective_always"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name", ["euler2d_p3", "ns2d_p2", "unstructured_ns2d_p2"])
 def test_newton_bdf2_step(L, mode, name, ortho):
     """One BDF1 then one BDF2 level to ||G|| <= 1e-8 ||G(U^n)||, compared with
     the oracle's Newton solution of the same stage equation solved to 1e-12,
-    with CGS2 (every Arnoldi column orthogonalised twice) and with the
-    selective second pass (at most as many second passes as columns)."""
+    with CGS2 (every Arnoldi column orthogonalised twice), with the selective
+    second pass (at most as many second passes as columns), and with the
+    selective scheme's criterion factor 1, which sends every column through
+    the not-accepted branch (a skipped update sweep, then the second pass)."""
     import torch
     m, eq, U0, _ = _case(name)
     disc = Discretization(m, _oeq(eq))
@@ -312,16 +314,18 @@ def test_newton_bdf2_step(L, mode, name, ortho):
     h = L.ldg_setup(m, eq)
     Un = torch.from_numpy(U0).cuda()
     U1 = torch.empty_like(Un)
-    st1 = L.ldg_newton_step(h, U1, Un, None, None, dt, L.solver_opts(mode=mode, first_step=True, ortho=ortho))
+    oo = {"ortho": L.ORTHO_CGS2 if ortho == "cgs2" else L.ORTHO_SELECTIVE,
+          "reorth_factor": 1.0 if ortho == "selective_always" else 0.0}
+    st1 = L.ldg_newton_step(h, U1, Un, None, None, dt, L.solver_opts(mode=mode, first_step=True, **oo))
     U2 = torch.empty_like(Un)
-    st2 = L.ldg_newton_step(h, U2, U1, Un, None, dt, L.solver_opts(mode=mode, force_rebuild=False, ortho=ortho))
+    st2 = L.ldg_newton_step(h, U2, U1, Un, None, dt, L.solver_opts(mode=mode, force_rebuild=False, **oo))
     for st in (st1, st2):
         assert st["res_final"] <= 1e-8 * st["res0"]
         assert st["newton_its"] <= 10
-        if ortho == L.ORTHO_CGS2:
-            assert st["reorth_its"] == st["gmres_its"]
-        else:
+        if ortho == "selective":
             assert 0 <= st["reorth_its"] <= st["gmres_its"]
+        else:
+            assert st["reorth_its"] == st["gmres_its"]
     d1 = np.abs(U1.cpu().numpy() - U1o).max() / np.abs(U1o).max()
     d2 = np.abs(U2.cpu().numpy() - U2o).max() / np.abs(U2o).max()
     assert d1 < 1e-7 and d2 < 1e-7, (d1, d2)
