@@ -97,6 +97,52 @@ def test_ilu0_reproduces_matrix_on_pattern():
     assert np.allclose(z[0], zz, atol=1e-12)
 
 
+@pytest.mark.parametrize("D,p", [(2, 4), (3, 2), (3, 3), (3, 4)])
+def test_ilu_apply_by_wavefront_levels_equals_row_order(D, p):
+    # the property a wavefront apply rests on: with level(i) = ix + iy + iz,
+    # every lower neighbour of row i in the line pattern lies on a lower
+    # level and every upper one on a higher level, so the rows of one level
+    # are independent in both triangular solves; solving level by level
+    # (every row of a level from the values of the earlier levels) gives the
+    # row-ordered solve of ilu_apply
+    rng = np.random.default_rng(7)
+    N, nc = p + 1, 3
+    pat = S.line_pattern(D, p)
+    npe = N ** D
+    lev = [i % N + (i // N) % N + (i // (N * N) if D == 3 else 0) for i in range(npe)]
+    for i in range(npe):
+        assert sum(k < i for k in pat[i]) == lev[i]   # the diagonal's slot is the level
+        for k in pat[i]:
+            if k < i:
+                assert lev[k] < lev[i]
+            elif k > i:
+                assert lev[k] > lev[i]
+    Ab = np.zeros((2, npe, npe, nc, nc))
+    for e in range(2):
+        for i in range(npe):
+            for j in pat[i]:
+                Ab[e, i, j] = 0.1 * rng.standard_normal((nc, nc))
+            Ab[e, i, i] += 3 * np.eye(nc)
+    F = S.ilu0(Ab, pat)
+    r = rng.standard_normal((2, nc, npe))
+    z_ref = S.ilu_apply(F, pat, r)
+    for e in range(2):
+        y = r[e].T.copy()
+        for l in range(1, max(lev) + 1):
+            rows = [i for i in range(npe) if lev[i] == l]
+            upd = {i: sum(F[e, i, k] @ y[k] for k in pat[i] if k < i) for i in rows}
+            for i in rows:
+                y[i] = y[i] - upd[i]
+        x = y.copy()
+        for l in range(max(lev), -1, -1):
+            rows = [i for i in range(npe) if lev[i] == l]
+            new = {i: np.linalg.solve(F[e, i, i], x[i] - sum((F[e, i, j] @ x[j] for j in pat[i] if j > i),
+                                                              np.zeros(nc))) for i in rows}
+            for i in rows:
+                x[i] = new[i]
+        assert np.allclose(x.T, z_ref[e], rtol=0, atol=1e-12 * np.abs(z_ref[e]).max())
+
+
 def test_ilu0_is_exact_lu_when_pattern_is_full():
     # with p = 1 in 1-D-like blocks (D=2, p=1 gives 3 of 4 couplings; use a
     # dense random block instead): ILU(0) on a full pattern equals LU
